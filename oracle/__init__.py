@@ -1,0 +1,212 @@
+"""Python face of the FP64 CPU oracle (oracle.c), via ctypes and numpy.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py, never by the product package.  Positions,
+velocities and forces are (N, 3) float64 arrays here.
+
+What each function follows in arXiv:2109.10876:
+  lj_energy / lj_force      Eq. 2 (LJ pair potential), F = -dV/dr (Eq. 1)
+  forces                    direct O(N^2) minimum-image pair sum under r < r_cut
+  forces_sample             the same sum for chosen particles only
+  pairs                     the Verlet pair set within r_cut + r_skin (Sec. 2.1.2)
+  vv_run                    velocity Verlet in two half steps (Fig. 1)
+  philox4x32_10             counter-based generator (Salmon et al., SC'11) for the
+                            Langevin noise (Sec. 4 names the thermostat only)
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_oracle
+
+_lib = None
+
+
+class OrcSystem(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("box", C.c_double * 3),
+        ("eps", C.c_double),
+        ("sigma", C.c_double),
+        ("rc", C.c_double),
+        ("shift", C.c_int32),
+        ("mass", C.c_double),
+        ("dt", C.c_double),
+        ("gamma", C.c_double),
+        ("kT", C.c_double),
+        ("seed", C.c_uint64),
+        ("n_bonds", C.c_int64),
+        ("bonds", C.POINTER(C.c_int32)),
+        ("fene_K", C.c_double),
+        ("fene_R0", C.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle.build()
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        sp = C.POINTER(OrcSystem)
+        L.orc_lj_energy.restype = C.c_double
+        L.orc_lj_energy.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_lj_force.restype = C.c_double
+        L.orc_lj_force.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_min_image_r2.restype = C.c_double
+        L.orc_min_image_r2.argtypes = [dp, dp, dp]
+        L.orc_forces.restype = C.c_int
+        L.orc_forces.argtypes = [sp, dp, dp, dp, dp]
+        L.orc_forces_sample.restype = C.c_int
+        L.orc_forces_sample.argtypes = [sp, dp, C.c_int64, C.POINTER(C.c_int64), dp, dp, dp]
+        L.orc_vv_run.restype = C.c_int
+        L.orc_vv_run.argtypes = [sp, dp, dp, dp, C.c_int64, C.c_int64, dp]
+        L.orc_pairs.restype = C.c_int64
+        L.orc_pairs.argtypes = [sp, dp, C.c_double, C.c_int64,
+                                C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.orc_philox4x32_10.restype = None
+        L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                        C.POINTER(C.c_uint32)]
+        L.orc_langevin_uniforms.restype = None
+        L.orc_langevin_uniforms.argtypes = [C.c_uint64, C.c_int64, C.c_int64, dp]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class System:
+    """Parameters of one periodic system (reduced units, Sec. 4: m = eps = sigma = 1).
+
+    rc is absolute (for the LJ fluid 2.5 sigma; for WCA 2**(1/6) sigma).
+    shift=True subtracts V(rc) so the pair energy is continuous at the cutoff.
+    """
+
+    def __init__(self, n, box, eps=1.0, sigma=1.0, rc=2.5, shift=True, mass=1.0,
+                 dt=0.005, gamma=0.0, kT=1.0, seed=0, bonds=None, fene_K=30.0,
+                 fene_R0=1.5):
+        self.n = int(n)
+        box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)).copy()
+        self.box = box
+        self.eps, self.sigma, self.rc, self.shift = float(eps), float(sigma), float(rc), bool(shift)
+        self.mass, self.dt, self.gamma, self.kT, self.seed = float(mass), float(dt), float(gamma), float(kT), int(seed)
+        self.bonds = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+        self.fene_K, self.fene_R0 = float(fene_K), float(fene_R0)
+
+    def c(self):
+        s = OrcSystem()
+        s.n = self.n
+        for k in range(3):
+            s.box[k] = self.box[k]
+        s.eps, s.sigma, s.rc, s.shift = self.eps, self.sigma, self.rc, int(self.shift)
+        s.mass, s.dt, s.gamma, s.kT, s.seed = self.mass, self.dt, self.gamma, self.kT, self.seed
+        if self.bonds is not None and len(self.bonds):
+            s.n_bonds = len(self.bonds)
+            s.bonds = self.bonds.ctypes.data_as(C.POINTER(C.c_int32))
+        else:
+            s.n_bonds = 0
+            s.bonds = C.POINTER(C.c_int32)()
+        s.fene_K, s.fene_R0 = self.fene_K, self.fene_R0
+        return s
+
+
+def lj_energy(r, eps=1.0, sigma=1.0):
+    return lib().orc_lj_energy(float(r), float(eps), float(sigma))
+
+
+def lj_force(r, eps=1.0, sigma=1.0):
+    return lib().orc_lj_force(float(r), float(eps), float(sigma))
+
+
+def min_image_r2(xi, xj, box):
+    xi, xj, box = _f64(xi, 3), _f64(xj, 3), _f64(box, 3)
+    return lib().orc_min_image_r2(_dp(xi), _dp(xj), _dp(box))
+
+
+def forces(sysm, x, v=None):
+    """Forces (N,3), and (U, K, W) for positions x (N,3). Raises on a broken bond."""
+    x = _f64(x, (sysm.n, 3))
+    F = np.zeros((sysm.n, 3))
+    euw = np.zeros(3)
+    vv = None if v is None else _f64(v, (sysm.n, 3))
+    s = sysm.c()
+    rc = lib().orc_forces(C.byref(s), _dp(x), None if vv is None else _dp(vv), _dp(F), _dp(euw))
+    if rc != 0:
+        raise RuntimeError(f"oracle forces failed: {rc}")
+    return F, euw
+
+
+def forces_sample(sysm, x, idx):
+    """Exact non-bonded forces on particles idx (each summed over all j).
+
+    Returns (F (n,3), U_i halves (n,), W_i halves (n,))."""
+    x = _f64(x, (sysm.n, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    F = np.zeros((len(idx), 3))
+    ui = np.zeros(len(idx))
+    wi = np.zeros(len(idx))
+    s = sysm.c()
+    rc = lib().orc_forces_sample(C.byref(s), _dp(x), len(idx),
+                                 idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(F), _dp(ui), _dp(wi))
+    if rc != 0:
+        raise RuntimeError(f"oracle forces_sample failed: {rc}")
+    return F, ui, wi
+
+
+def vv_run(sysm, x, v, nsteps, step0=0, thermo=False):
+    """Velocity Verlet from (x, v); returns (x, v, F[, thermo (nsteps,3)])."""
+    x = _f64(x, (sysm.n, 3)).copy()
+    v = _f64(v, (sysm.n, 3)).copy()
+    F = np.zeros((sysm.n, 3))
+    th = np.zeros((max(int(nsteps), 1), 3)) if thermo else None
+    s = sysm.c()
+    rc = lib().orc_vv_run(C.byref(s), _dp(x), _dp(v), _dp(F), int(step0), int(nsteps),
+                          None if th is None else _dp(th))
+    if rc != 0:
+        raise RuntimeError(f"oracle vv_run failed: {rc}")
+    if thermo:
+        return x, v, F, th[:nsteps]
+    return x, v, F
+
+
+def pairs(sysm, x, r):
+    """Brute-force pair set {(i, j): i < j, |d_ij| < r}, lexicographic, and per-particle counts."""
+    x = _f64(x, (sysm.n, 3))
+    s = sysm.c()
+    counts = np.zeros(sysm.n, dtype=np.int32)
+    m = lib().orc_pairs(C.byref(s), _dp(x), float(r), 0, None,
+                        counts.ctypes.data_as(C.POINTER(C.c_int32)))
+    out = np.zeros((max(m, 1), 2), dtype=np.int32)
+    m2 = lib().orc_pairs(C.byref(s), _dp(x), float(r), m,
+                         out.ctypes.data_as(C.POINTER(C.c_int32)), None)
+    assert m2 == m
+    return out[:m], counts
+
+
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(t) & 0xFFFFFFFF for t in ctr])
+    k = (C.c_uint32 * 2)(*[int(t) & 0xFFFFFFFF for t in key])
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(o[i]) for i in range(4)]
+
+
+def langevin_uniforms(seed, pid, step):
+    u = np.zeros(3)
+    lib().orc_langevin_uniforms(int(seed), int(pid), int(step), _dp(u))
+    return u
+
+
+def num_threads():
+    return lib().orc_num_threads()

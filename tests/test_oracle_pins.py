@@ -1,0 +1,300 @@
+"""Pins for the FP64 CPU oracle, against facts that do not come from the oracle.
+
+Each test checks the oracle against a closed form, a symbolic derivative, a
+lattice sum by integer enumeration, a conservation law, an ODE solution from
+an independent integrator, or a published known-answer vector, chosen so that
+a dropped term, a wrong sign or factor, or a swapped operand fails one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle
+from paper_2109_10876_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RC = 2.5
+SKIN = 0.3
+
+
+# ---------------------------------------------------------------- Eq. 2 pins
+def test_lj_closed_forms():
+    """V(sigma)=0, F(sigma)=24 eps/sigma, minimum V=-eps with F=0 at 2^(1/6) sigma."""
+    for eps, sig in [(1.0, 1.0), (0.9, 1.05), (1.1, 0.95)]:
+        assert abs(oracle.lj_energy(sig, eps, sig)) < 1e-14
+        assert oracle.lj_force(sig, eps, sig) == pytest.approx(24.0 * eps / sig, rel=1e-14)
+        rm = 2 ** (1 / 6) * sig
+        assert oracle.lj_energy(rm, eps, sig) == pytest.approx(-eps, rel=1e-14)
+        assert abs(oracle.lj_force(rm, eps, sig)) < 1e-12
+
+
+def test_lj_force_is_symbolic_derivative():
+    """Force magnitude equals -dV/dr of Eq. 2 from sympy at many r, eps, sigma."""
+    r, e, s = sp.symbols("r e s", positive=True)
+    V = 4 * e * ((s / r) ** 12 - (s / r) ** 6)
+    dV = sp.lambdify((r, e, s), -sp.diff(V, r), "mpmath")
+    Vl = sp.lambdify((r, e, s), V, "mpmath")
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        rr, ee, ss = rng.uniform(0.8, 3.0), rng.uniform(0.5, 2.0), rng.uniform(0.8, 1.2)
+        assert oracle.lj_force(rr, ee, ss) == pytest.approx(float(dV(rr, ee, ss)), rel=1e-12, abs=1e-14)
+        assert oracle.lj_energy(rr, ee, ss) == pytest.approx(float(Vl(rr, ee, ss)), rel=1e-12, abs=1e-14)
+    # value at the LJ-fluid cutoff used by every LJ workload
+    assert oracle.lj_force(2.5) == pytest.approx(-0.0389995, abs=5e-8)
+    assert oracle.lj_energy(2.5) == pytest.approx(-0.0163169, abs=5e-8)
+
+
+def test_min_image_matches_image_enumeration():
+    """Minimum-image r^2 equals the smallest r^2 over the 27 periodic images."""
+    rng = np.random.default_rng(1)
+    for _ in range(500):
+        box = rng.uniform(5.0, 12.0, size=3)
+        xi, xj = rng.uniform(0, 1, 3) * box, rng.uniform(0, 1, 3) * box
+        best = min(float(np.sum((xi - xj - np.array(s) * box) ** 2))
+                   for s in itertools.product((-1, 0, 1), repeat=3))
+        assert oracle.min_image_r2(xi, xj, box) == pytest.approx(best, rel=1e-13)
+
+
+# ------------------------------------------------- tiny boxes by brute force
+def test_two_particles_across_boundary():
+    """Two particles separated across the periodic boundary: force along d,
+    magnitude -dV/dr, equal and opposite; energy shifted to 0 at the cutoff."""
+    box = np.array([10.0, 9.0, 8.0])
+    x = np.array([[0.2, 4.0, 7.9], [9.4, 4.3, 0.1]])
+    s = oracle.System(2, box, rc=RC)
+    F, euw = oracle.forces(s, x)
+    d = np.array([0.2 - 9.4 + 10.0, 4.0 - 4.3, 7.9 - 0.1 - 8.0])
+    r = np.linalg.norm(d)
+    fm = 24 * (2 * r ** -13 - r ** -7)
+    np.testing.assert_allclose(F[0], fm * d / r, rtol=1e-13)
+    np.testing.assert_allclose(F[1], -F[0], rtol=0, atol=0)
+    V = 4 * (r ** -12 - r ** -6) - 4 * (RC ** -12 - RC ** -6)
+    assert euw[0] == pytest.approx(V, rel=1e-13)
+    assert euw[2] == pytest.approx(fm * r, rel=1e-13)   # virial d . f = r * f(r)
+
+
+def test_cutoff_is_strict_and_particle_at_box_edge():
+    box = np.array([8.0, 8.0, 8.0])
+    L = 8.0
+    # at exactly r = rc: no interaction (strict r < r_cut); just inside: interaction
+    x = np.array([[1.0, 1.0, 1.0], [1.0 + RC, 1.0, 1.0]])
+    F, _ = oracle.forces(oracle.System(2, box, rc=RC), x)
+    assert np.all(F == 0.0)
+    x[1, 0] = 1.0 + RC - 1e-9
+    F, _ = oracle.forces(oracle.System(2, box, rc=RC), x)
+    # attractive at r ~ 2.5: particle 0 is pulled towards particle 1 (+x)
+    assert F[0, 0] == pytest.approx(-oracle.lj_force(RC - 1e-9), rel=1e-9) and F[1, 0] == -F[0, 0]
+    # a particle at the largest double below L interacts with one at 0.5
+    x = np.array([[np.nextafter(L, 0), 2.0, 2.0], [0.5, 2.0, 2.0]])
+    F, _ = oracle.forces(oracle.System(2, box, rc=RC), x)
+    r = 0.5 + (L - np.nextafter(L, 0))
+    assert F[1, 0] == pytest.approx(24 * (2 * r ** -13 - r ** -7), rel=1e-12)
+
+
+def test_pair_set_matches_image_enumeration():
+    """Pair set within r_cut + r_skin equals an enumeration over images."""
+    rng = np.random.default_rng(2)
+    for n in (3, 8, 40):
+        box = np.array([6.0, 6.5, 7.0])
+        x = rng.uniform(0, 1, (n, 3)) * box
+        s = oracle.System(n, box, rc=RC)
+        got, counts = oracle.pairs(s, x, RC + SKIN)
+        want = []
+        for i in range(n):
+            for j in range(i + 1, n):
+                m = min(float(np.sum((x[i] - x[j] - np.array(t) * box) ** 2))
+                        for t in itertools.product((-1, 0, 1), repeat=3))
+                if m < (RC + SKIN) ** 2:
+                    want.append((i, j))
+        assert [tuple(p) for p in got] == want
+        assert counts.sum() == 2 * len(want)
+
+
+# ------------------------------------------------------------- fcc lattice pins
+def _fcc_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "fcc_shells.txt")) if l[0] != "#"]
+    return [(int(m), float(d), int(c)) for m, d, c in rows]
+
+
+def test_fcc_shells_golden_is_lattice_fact():
+    a = (4 / 0.8442) ** (1 / 3)
+    for m, d, c in _fcc_golden():
+        assert a * math.sqrt(m / 2) == pytest.approx(d, abs=5e-7)
+    B = inputs.FCC_BASIS
+    dist = {}
+    for n in itertools.product(range(-2, 3), repeat=3):
+        for b in B:
+            v = (np.array(n) + b)
+            m = int(round(2 * v @ v))
+            if m:
+                dist[m] = dist.get(m, 0) + 1
+    assert [dist[m] for m in range(1, 7)] == [c for _, _, c in _fcc_golden()]
+
+
+def test_fcc_4000_pins():
+    """N = 4000 fcc at rho = 0.8442: 54 / 78 neighbours, 108000 / 156000 pairs,
+    zero net force per site, U/N = -6.3328120 with the shifted potential."""
+    x, box = inputs.fcc_lattice(10, 0.8442)
+    assert len(x) == 4000
+    s = oracle.System(4000, box, rc=RC)
+    pr, counts = oracle.pairs(s, x, RC)
+    assert len(pr) == 108000 and np.all(counts == 54)
+    pl, countsl = oracle.pairs(s, x, RC + SKIN)
+    assert len(pl) == 156000 and np.all(countsl == 78)
+    F, euw = oracle.forces(s, x)
+    assert np.max(np.abs(F)) < 1e-11
+    assert euw[0] / 4000 == pytest.approx(-6.3328120, abs=5e-8)
+    # the same number from the shell table: 1/2 sum_shells count (V(r) - V(rc))
+    Vs = lambda r: 4 * (r ** -12 - r ** -6) - 4 * (RC ** -12 - RC ** -6)
+    shell = 0.5 * sum(c * Vs((4 / 0.8442) ** (1 / 3) * math.sqrt(m / 2))
+                      for m, _, c in _fcc_golden() if m <= 4)
+    assert euw[0] / 4000 == pytest.approx(shell, rel=1e-12)
+
+
+def test_cell_rule_from_paper():
+    """N = 262144 at rho = 0.8442 gives a 24^3 cell grid with cell edge >= r_cut + r_skin
+    (Sec. 5 quotes the (24, 24, 24) grid)."""
+    L = (262144 / 0.8442) ** (1 / 3)
+    assert math.floor(L / (RC + SKIN)) == 24
+
+
+# ------------------------------------------------------------------ invariants
+def _liquid(ncell=5, seed=3, amp=0.15):
+    x, v, box = inputs.perturbed_lattice(ncell, seed=seed, amp=amp)
+    return x, v, box
+
+
+def test_newton_third_law_and_force_is_minus_grad_U():
+    x, v, box = _liquid()
+    n = len(x)
+    s = oracle.System(n, box, rc=RC)
+    F, euw = oracle.forces(s, x)
+    assert np.max(np.abs(F.sum(axis=0))) < 1e-12 * np.max(np.abs(F)) * n
+    # F = -grad U (Eq. 1) by central differences of the shifted energy
+    rng = np.random.default_rng(4)
+    h = 1e-6
+    for i in rng.choice(n, 6, replace=False):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            up = oracle.forces(s, xp)[1][0]
+            um = oracle.forces(s, xm)[1][0]
+            assert F[i, k] == pytest.approx(-(up - um) / (2 * h), abs=2e-5 * max(1, abs(F[i, k])))
+
+
+def test_virial_scaling_identity():
+    """With r_cut = 2.5 sigma scaling with sigma and V shifted to zero at r_cut,
+    U depends on sigma only through r / sigma, so sigma dU/dsigma = W (the
+    virial sum of d . f), and eps dU/deps = U."""
+    x, v, box = _liquid(seed=5)
+    n = len(x)
+    sig, h = 1.0, 1e-6
+    U0, W0 = oracle.forces(oracle.System(n, box, sigma=sig, rc=RC * sig), x)[1][[0, 2]]
+    Up = oracle.forces(oracle.System(n, box, sigma=sig + h, rc=RC * (sig + h)), x)[1][0]
+    Um = oracle.forces(oracle.System(n, box, sigma=sig - h, rc=RC * (sig - h)), x)[1][0]
+    assert sig * (Up - Um) / (2 * h) == pytest.approx(W0, rel=1e-6)
+    Ue = oracle.forces(oracle.System(n, box, eps=1.3, rc=RC), x)[1][0]
+    assert Ue == pytest.approx(1.3 * U0, rel=1e-13)
+
+
+def test_nve_conservation_and_reversibility():
+    """Velocity Verlet (Fig. 1): momentum conserved, the energy error is
+    second order in dt (ratio ~4 when dt halves) and small, and the map is
+    time-reversible."""
+    x, v, box = inputs.lj_fluid(5, T=0.72, seed=6)
+    n = len(x)
+    dE = []
+    for dt in (0.005, 0.0025):
+        s = oracle.System(n, box, rc=RC, dt=dt)
+        F0, e0 = oracle.forces(s, x, v)
+        E0 = e0[0] + e0[1]
+        x1, v1, F1, th = oracle.vv_run(s, x, v, int(round(0.5 / dt)), thermo=True)
+        E = th[:, 0] + th[:, 1]
+        dE.append(np.max(np.abs(E - E0)) / n)
+        assert np.max(np.abs(v1.sum(axis=0))) < 1e-10
+    assert dE[0] < 1e-3
+    assert 3.0 < dE[0] / dE[1] < 5.0
+    # reverse: negate v, run the same steps back, negate again -> initial state
+    s = oracle.System(n, box, rc=RC, dt=0.005)
+    x1, v1, _ = oracle.vv_run(s, x, v, 100)
+    x2, v2, _ = oracle.vv_run(s, x1, -v1, 100)
+    d = x2 - x
+    d -= box * np.round(d / box)
+    assert np.max(np.abs(d)) < 1e-9
+    assert np.max(np.abs(-v2 - v)) < 1e-9
+
+
+def test_velocity_verlet_is_second_order_against_ode_solver():
+    """Two LJ particles: the oracle's trajectory converges to scipy's DOP853
+    solution of m x'' = F with error ratio ~4 when dt halves."""
+    from scipy.integrate import solve_ivp
+    box = np.array([20.0, 20.0, 20.0])
+    x0 = np.array([[5.0, 5.0, 5.0], [6.15, 5.3, 5.1]])
+    v0 = np.array([[0.3, -0.2, 0.1], [-0.3, 0.2, -0.1]])
+    T = 0.64
+
+    def rhs(t, y):
+        p = y[:6].reshape(2, 3)
+        d = p[0] - p[1]
+        r = np.linalg.norm(d)
+        f = 24 * (2 * r ** -13 - r ** -7) * d / r if r < RC else 0 * d
+        return np.concatenate([y[6:], f, -f])
+
+    sol = solve_ivp(rhs, (0, T), np.concatenate([x0.ravel(), v0.ravel()]), method="DOP853",
+                    rtol=1e-12, atol=1e-12)
+    xe = sol.y[:6, -1].reshape(2, 3)
+    errs = []
+    for dt in (0.004, 0.002, 0.001):
+        s = oracle.System(2, box, rc=RC, dt=dt)
+        x1, v1, _ = oracle.vv_run(s, x0, v0, int(round(T / dt)))
+        errs.append(np.max(np.abs(x1 - xe)))
+    assert errs[2] < 1e-4
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+# ------------------------------------------------------------------ FENE, Langevin
+def test_fene_matches_symbolic_derivative_and_breaks():
+    r, K, R0 = sp.symbols("r K R0", positive=True)
+    U = -sp.Rational(1, 2) * K * R0 ** 2 * sp.log(1 - r ** 2 / R0 ** 2)
+    f = sp.lambdify((r, K, R0), -sp.diff(U, r), "mpmath")
+    Ul = sp.lambdify((r, K, R0), U, "mpmath")
+    box = np.array([10.0, 10.0, 10.0])
+    for rr in (0.5, 0.97, 1.2, 1.45):
+        x = np.array([[1.0, 2.0, 3.0], [1.0 + rr * 0.6, 2.0 + rr * 0.8, 3.0]])
+        s = oracle.System(2, box, rc=1e-3, shift=False, bonds=[[0, 1]], fene_K=30, fene_R0=1.5)
+        F, euw = oracle.forces(s, x)
+        d = x[0] - x[1]
+        np.testing.assert_allclose(F[0], float(f(rr, 30, 1.5)) * d / rr, rtol=1e-12)
+        np.testing.assert_allclose(F[1], -F[0], rtol=1e-15)
+        assert euw[0] == pytest.approx(float(Ul(rr, 30, 1.5)), rel=1e-12)
+    x = np.array([[1.0, 2.0, 3.0], [2.6, 2.0, 3.0]])
+    with pytest.raises(RuntimeError):
+        oracle.forces(oracle.System(2, box, rc=1e-3, bonds=[[0, 1]], fene_R0=1.5), x)
+
+
+def test_philox_known_answers():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(t, 16) for t in line.split()]
+        assert oracle.philox4x32_10(w[0:4], w[4:6]) == w[6:10]
+
+
+def test_langevin_uniforms_moments_and_thermostat_temperature():
+    u = np.array([oracle.langevin_uniforms(7, i, s) for i in range(200) for s in range(50)])
+    assert np.all(np.abs(u) < 0.5)
+    assert abs(u.mean()) < 0.01 and u.var() == pytest.approx(1 / 12, rel=0.03)
+    # ideal gas (no pair forces within a tiny cutoff) under the thermostat: <T> -> kT
+    n = 64
+    box = np.array([20.0, 20.0, 20.0])
+    x = inputs.random_gas(n, box, seed=8)
+    v = np.zeros((n, 3))
+    s = oracle.System(n, box, rc=1e-3, dt=0.01, gamma=1.0, kT=1.3, seed=9)
+    x, v, F, th = oracle.vv_run(s, x, v, 4000, thermo=True)
+    T = 2 * th[1000:, 1] / (3 * n)
+    assert T.mean() == pytest.approx(1.3, rel=0.06)
