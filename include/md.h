@@ -1,0 +1,159 @@
+/*
+ * md.h -- C ABI of the GB300 short-range molecular-dynamics library.
+ *
+ * The library integrates Newton's equations m r'' = F, F = -grad U (Eq. 1 of
+ * arXiv:2109.10876, Sec. 2.1) for particles in orthorhombic periodic boxes,
+ * with the Lennard-Jones pair potential of Eq. 2 truncated at r < r_cut
+ * (Sec. 2.1.1), or its repulsive WCA form (r_cut = 2^(1/6) sigma, Sec. 4),
+ * optional FENE bonds and a Langevin thermostat (Sec. 4), using cell binning
+ * and Verlet lists with a skin, r_cell >= r_cut + r_skin (Sec. 2.1.2), and
+ * velocity Verlet in two half steps (Fig. 1).
+ *
+ * Every step runs in hand-written sm_103a CUDA kernels; there is no CPU path.
+ *
+ * Conventions for every entry point:
+ *   - Per-particle arrays use the component-major layout a[k * N + i]
+ *     (k = 0, 1, 2 for x, y, z; N = total particles over all replicas),
+ *     i.e. a (3, N) row-major array; particle i is the i-th particle the
+ *     caller passed to md_set_state.
+ *   - Array arguments may be device pointers or host pointers (pageable or
+ *     pinned); the library copies through them and never keeps or frees them.
+ *     The caller owns all memory it passes in.  The library owns everything it
+ *     allocates (cells, lists, flags, its copy of the state) and frees it in
+ *     md_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - Argument errors are returned synchronously.  Errors found on the device
+ *     (list overflow, non-finite values, broken bonds, fixed-point overflow)
+ *     are latched in an error word and returned by the next synchronising
+ *     call (md_get_stats, md_export_pairs, md_get_state, md_sync).
+ *   - Units are reduced LJ units (Sec. 4: m = eps = sigma = 1 by default).
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_handle md_handle;
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_ARG = -1,            /* invalid argument or call order            */
+    MD_ERR_CUDA = -2,           /* a CUDA runtime call failed                */
+    MD_ERR_LIST_OVERFLOW = -3,  /* a particle had more neighbours than the list holds */
+    MD_ERR_NONFINITE = -4,      /* a non-finite position, velocity or force  */
+    MD_ERR_BOND_BROKEN = -5,    /* a FENE bond reached r >= R0               */
+    MD_ERR_FIXED_OVERFLOW = -6, /* a pair force exceeded the fixed-point range */
+    MD_ERR_TIMEOUT = -7,        /* a bounded device wait gave up             */
+    MD_ERR_BOX_TOO_SMALL = -8   /* a box edge is shorter than 2 (r_cut + r_skin) */
+} md_status;
+
+enum { MD_LJ = 0, MD_WCA = 1 };            /* md_params.potential */
+enum { MD_FP64 = 0, MD_FP32_FIXED = 1 };   /* md_params.precision */
+
+/* Parameters of a set of independent replicas (n_replicas >= 1).  Replica r
+ * holds particles [replica_offsets[r], replica_offsets[r+1]) of the arrays
+ * passed to md_set_state.  All pointers here are HOST pointers, read during
+ * md_create only. */
+typedef struct {
+    int32_t n_replicas;
+    const int64_t *replica_offsets; /* n_replicas + 1, offsets[0] = 0           */
+    const double *box;              /* 3 per replica: Lx, Ly, Lz                */
+    const double *eps;              /* per replica, Eq. 2 epsilon               */
+    const double *sigma;            /* per replica, Eq. 2 sigma                 */
+    double rc_over_sigma;           /* cutoff in units of sigma (LJ fluid: 2.5);
+                                       ignored for MD_WCA (2^(1/6))             */
+    double skin;                    /* Verlet skin r_skin (absolute)            */
+    double dt;                      /* time step                                */
+    double mass;                    /* particle mass                            */
+    int32_t potential;              /* MD_LJ (shifted to 0 at r_cut) or MD_WCA  */
+    int32_t precision;              /* MD_FP32_FIXED or MD_FP64                 */
+    double langevin_gamma;          /* 0 = NVE                                  */
+    double kT;                      /* Langevin temperature                     */
+    uint64_t seed;                  /* Langevin noise key (Philox4x32-10)       */
+    double fene_K, fene_R0;         /* FENE bond constants                      */
+    int64_t n_bonds;                /* FENE bonds                               */
+    const int32_t *bonds;           /* 2 * n_bonds particle indices, or NULL    */
+    int32_t list_capacity;          /* neighbours per particle; 0 = automatic   */
+    int32_t reserved0;
+} md_params;
+
+/* Counters and diagnostics (md_get_stats). */
+typedef struct {
+    int64_t steps;              /* steps integrated since md_set_state        */
+    int64_t rebuilds;           /* neighbour-list builds since md_set_state   */
+    int64_t list_entries;       /* sum of list lengths at the last build      */
+    int32_t max_list_len;       /* longest list at the last build             */
+    int32_t list_capacity;      /* current capacity per particle              */
+    int32_t max_cell_occupancy; /* at the last build                          */
+    int32_t error_word;         /* latched device error bits                  */
+    int32_t ncell[3];           /* cell grid of replica 0                     */
+    int32_t n_replicas;
+    int64_t n_particles;
+} md_stats;
+
+/* Create a handle for the replicas described by p (Sec. 2.1: cells of edge
+ * >= r_cut + r_skin per box).  Synchronous.  Returns MD_ERR_BOX_TOO_SMALL when a
+ * box edge is shorter than 2 (r_cut + r_skin), MD_ERR_ARG for inconsistent
+ * parameters, MD_ERR_CUDA if device memory cannot be allocated.  *out is set to
+ * NULL on failure. */
+md_status md_create(const md_params *p, md_handle **out);
+
+/* Free everything the handle owns.  Synchronises the device first. */
+void md_destroy(md_handle *h);
+
+/* Load positions x and velocities v, each (3, N) component-major FP64, into the
+ * handle; positions are wrapped into [0, L).  Resets the step counter, marks
+ * the neighbour list stale and the stored force invalid.  Asynchronous. */
+md_status md_set_state(md_handle *h, const double *x, const double *v, void *stream);
+
+/* Copy the current positions and velocities out, (3, N) FP64 each, in the
+ * caller's particle order.  Either pointer may be NULL.  Synchronises `stream`
+ * and returns any latched device error. */
+md_status md_get_state(md_handle *h, double *x, double *v, void *stream);
+
+/* Bin particles into cells with a counting sort and rebuild the Verlet list of
+ * all pairs with |d| < r_cut + r_skin (Sec. 2.1.2), now, whatever the
+ * displacement since the last build.  Asynchronous. */
+md_status md_build_neighbors(md_handle *h, void *stream);
+
+/* Evaluate the conservative forces (pair potential of Eq. 2 under r < r_cut,
+ * plus FENE bonds) at the current positions.  f_out (may be NULL) receives the
+ * (3, N) FP64 forces in the caller's order; euw_out (may be NULL) receives
+ * (U, K, W) per replica, 3 * n_replicas FP64: potential energy (pair energy
+ * shifted to 0 at r_cut, plus FENE), kinetic energy 1/2 m sum v^2, and the
+ * virial sum over pairs of d_ij . f_ij.  Rebuilds the list first if particles
+ * moved more than r_skin / 2 since the last build.  Asynchronous. */
+md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *stream);
+
+/* Advance nsteps velocity-Verlet steps (Fig. 1: half kick + drift, force,
+ * half kick), rebuilding the cells and the Verlet list on the device whenever
+ * some particle has moved more than r_skin / 2 since the last build.  If
+ * thermo_every > 0, thermo_out receives (U, K, W) per replica after every
+ * thermo_every-th step: floor(nsteps / thermo_every) records of 3 * n_replicas
+ * FP64 each.  Asynchronous; device errors are latched. */
+md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream);
+
+/* Export the current Verlet pair set as pairs (i, j), i < j, in the caller's
+ * particle numbering, in no particular order.  Writes at most `capacity` pairs
+ * (2 * capacity int32) to pairs_out and the total count to *n_out (host).
+ * Synchronises `stream`. */
+md_status md_export_pairs(md_handle *h, int32_t *pairs_out, int64_t capacity, int64_t *n_out, void *stream);
+
+/* Wait for all work on `stream` and return any latched device error. */
+md_status md_sync(md_handle *h, void *stream);
+
+/* Counters and latched errors; synchronises the device. */
+md_status md_get_stats(md_handle *h, md_stats *out);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next call. */
+const char *md_last_error(const md_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_GB300_H */

@@ -1,0 +1,520 @@
+// Host side of the C ABI declared in include/md.h: parameter checks, the
+// cell grid of every replica (edge >= r_cut + r_skin, Sec. 2.1.2 of
+// arXiv:2109.10876), device allocations owned by the handle, and the kernel
+// sequence of one velocity-Verlet step (Fig. 1).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "md.h"
+#include "md_internal.cuh"
+
+using mdk::Bufs;
+using mdk::Ctl;
+using mdk::Replica;
+
+struct md_handle {
+    md_params p{};
+    std::vector<Replica> reps;
+    std::vector<int64_t> offsets;
+    Bufs b{};
+    std::vector<void *> allocs;
+    int precision = 1;
+    bool auto_capacity = true;
+    bool state_set = false;
+    bool F_valid = false;
+    long long N = 0, S = 0;
+    int C = 0, nblk = 0, K = 0;
+    double *stage = nullptr;        // 6 * N doubles: in/out staging
+    double *thermo_stage = nullptr; // grows on demand
+    long long thermo_cap = 0;
+    unsigned long long *d_count = nullptr;
+    std::string err;
+};
+
+namespace {
+
+md_status fail(md_handle *h, md_status s, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+bool cuda_ok(md_handle *h, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return true;
+    if (h) h->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+}
+
+template <class T>
+T *dalloc(md_handle *h, size_t count)
+{
+    void *p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+    h->allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+double lj_v(double r, double eps, double sig)
+{
+    double s6 = std::pow(sig / r, 6.0);
+    return 4.0 * eps * (s6 * s6 - s6);
+}
+
+double lj_fmag(double r, double eps, double sig)
+{
+    double s6 = std::pow(sig / r, 6.0);
+    return 24.0 * eps * (2.0 * s6 * s6 - s6) / r;
+}
+
+long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
+
+// Map latched device error bits to a status.
+md_status status_of(md_handle *h, int bits)
+{
+    if (!bits) return MD_OK;
+    if (bits & mdk::kErrList) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list capacity exceeded");
+    if (bits & mdk::kErrBond) return fail(h, MD_ERR_BOND_BROKEN, "FENE bond reached r >= R0");
+    if (bits & mdk::kErrFixed) return fail(h, MD_ERR_FIXED_OVERFLOW, "pair force outside the fixed-point range");
+    if (bits & mdk::kErrNonfinite) return fail(h, MD_ERR_NONFINITE, "non-finite position, velocity or force");
+    if (bits & mdk::kErrTimeout) return fail(h, MD_ERR_TIMEOUT, "bounded device wait timed out");
+    return fail(h, MD_ERR_CUDA, "unknown device error bits");
+}
+
+md_status read_ctl(md_handle *h, Ctl *out)
+{
+    if (!cuda_ok(h, cudaMemcpy(out, h->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost), "read control block"))
+        return MD_ERR_CUDA;
+    return MD_OK;
+}
+
+md_status alloc_list(md_handle *h, int K)
+{
+    if (h->b.nbr) {
+        for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+            if (*it == h->b.nbr) { cudaFree(*it); h->allocs.erase(it); break; }
+        h->b.nbr = nullptr;
+    }
+    h->K = K;
+    h->b.K = K;
+    h->b.nbr = dalloc<int>(h, (size_t)K * (size_t)h->S);
+    if (!h->b.nbr) return fail(h, MD_ERR_CUDA, "cannot allocate the neighbour list");
+    return MD_OK;
+}
+
+md_status ensure_thermo(md_handle *h, long long count)
+{
+    if (h->thermo_cap >= count) return MD_OK;
+    if (h->thermo_stage) {
+        for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+            if (*it == h->thermo_stage) { cudaFree(*it); h->allocs.erase(it); break; }
+        h->thermo_stage = nullptr;
+        h->thermo_cap = 0;
+    }
+    h->thermo_stage = dalloc<double>(h, (size_t)count);
+    if (!h->thermo_stage) return fail(h, MD_ERR_CUDA, "cannot allocate thermo buffer");
+    h->thermo_cap = count;
+    return MD_OK;
+}
+
+md_status sync_and_check(md_handle *h, cudaStream_t st)
+{
+    if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
+    if (!cuda_ok(h, cudaGetLastError(), "kernel launch")) return MD_ERR_CUDA;
+    Ctl c;
+    md_status s = read_ctl(h, &c);
+    if (s != MD_OK) return s;
+    return status_of(h, c.err);
+}
+
+}  // namespace
+
+extern "C" {
+
+md_status md_create(const md_params *p, md_handle **out)
+{
+    if (!out) return MD_ERR_ARG;
+    *out = nullptr;
+    if (!p || p->n_replicas < 1 || p->n_replicas > mdk::kMaxReplicas || !p->replica_offsets || !p->box ||
+        !p->eps || !p->sigma)
+        return MD_ERR_ARG;
+    if (!(p->dt > 0) || !(p->mass > 0) || !(p->skin >= 0) || (p->potential != MD_LJ && p->potential != MD_WCA) ||
+        (p->precision != MD_FP64 && p->precision != MD_FP32_FIXED) || p->langevin_gamma < 0 ||
+        (p->potential == MD_LJ && !(p->rc_over_sigma > 0)) || p->list_capacity < 0 || p->n_bonds < 0 ||
+        (p->n_bonds > 0 && (!p->bonds || !(p->fene_K > 0) || !(p->fene_R0 > 0))) ||
+        (p->langevin_gamma > 0 && !(p->kT >= 0)))
+        return MD_ERR_ARG;
+    if (p->replica_offsets[0] != 0) return MD_ERR_ARG;
+    md_handle *h = new md_handle();
+    h->p = *p;
+    h->precision = p->precision;
+    const int nrep = p->n_replicas;
+    h->offsets.assign(p->replica_offsets, p->replica_offsets + nrep + 1);
+    long long slot = 0;
+    int cell = 0;
+    for (int r = 0; r < nrep; ++r) {
+        long long n = h->offsets[r + 1] - h->offsets[r];
+        if (n < 0 || n > (1LL << 30)) { delete h; return MD_ERR_ARG; }
+        Replica R{};
+        const double eps = p->eps[r], sig = p->sigma[r];
+        if (!(eps > 0) || !(sig > 0)) { delete h; return MD_ERR_ARG; }
+        const double rc = (p->potential == MD_WCA ? std::pow(2.0, 1.0 / 6.0) : p->rc_over_sigma) * sig;
+        const double rl = rc + p->skin;
+        double Lmax = 0;
+        for (int k = 0; k < 3; ++k) {
+            const double L = p->box[3 * r + k];
+            if (!(L > 0) || !std::isfinite(L)) { delete h; return MD_ERR_ARG; }
+            if (L < 2.0 * rl) {
+                delete h;
+                return MD_ERR_BOX_TOO_SMALL;
+            }
+            Lmax = std::fmax(Lmax, L);
+            R.L[k] = L;
+            R.to_q[k] = 4294967296.0 / L;
+            R.from_q[k] = L / 4294967296.0;
+            R.qs[k] = (float)(L / 4294967296.0);
+            // cell edge L / n >= r_cut + r_skin, with a margin far above the
+            // fixed-point quantisation so that the 27-cell search is complete
+            int nc = (int)std::floor(L / (rl * (1.0 + 1e-6) + 4.0 * L / 4294967296.0));
+            R.ncell[k] = nc < 1 ? 1 : nc;
+        }
+        if ((long long)R.ncell[0] * R.ncell[1] * R.ncell[2] > (1LL << 28)) { delete h; return MD_ERR_ARG; }
+        R.cell_off = cell;
+        R.ncells = R.ncell[0] * R.ncell[1] * R.ncell[2];
+        cell += R.ncells;
+        R.slot_begin = slot;
+        R.n = n;
+        R.id_begin = h->offsets[r];
+        R.blk_begin = (int)(slot / mdk::kBlock);
+        slot += round_up(n, mdk::kBlock);
+        R.blk_end = (int)(slot / mdk::kBlock);
+        R.eps = eps;
+        R.sigma = sig;
+        R.rc = rc;
+        R.rc2 = rc * rc;
+        R.vshift = lj_v(rc, eps, sig);
+        R.rl2 = rl * rl;
+        R.eps24_f = (float)(24.0 * eps);
+        R.eps4_f = (float)(4.0 * eps);
+        R.sig2_f = (float)(sig * sig);
+        R.rc2_f = (float)(rc * rc);
+        R.vshift_f = (float)R.vshift;
+        // bands around the cutoffs inside which the FP32 r^2 cannot decide:
+        // fixed-point quantisation (|dd| <= sqrt(3) L / 2^32) plus FP32 rounding
+        const double qd = std::sqrt(3.0) * Lmax / 4294967296.0;
+        const double brc = 2.0 * rc * qd + std::ldexp(1.0, -16) * rc * rc;
+        const double brl = 2.0 * rl * qd + std::ldexp(1.0, -16) * rl * rl;
+        R.rc2_lo = (float)(rc * rc - brc);
+        R.rc2_hi = (float)(rc * rc + brc);
+        R.rl2_lo = (float)(rl * rl - brl);
+        R.rl2_hi = (float)(rl * rl + brl);
+        double half = 0.5 * p->skin * (1.0 - 1e-6) - 2.0 * qd;
+        R.disp2_thr = (float)std::fmax(half * half, 1e-30);
+        // smallest r^2 at which one pair-force component stays below 2^21
+        double lo = 1e-3 * sig, hi = rc;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (lj_fmag(mid, eps, sig) > std::ldexp(1.0, 21) * 0.9) lo = mid; else hi = mid;
+        }
+        R.fmax2 = (float)(hi * hi);
+        h->reps.push_back(R);
+    }
+    h->N = h->offsets[nrep];
+    h->S = slot;
+    h->C = cell;
+    h->nblk = (int)(slot / mdk::kBlock);
+    if (h->N < 1) { delete h; return MD_ERR_ARG; }
+
+    // FENE bonds must join two distinct particles of the same replica
+    for (int64_t q = 0; q < p->n_bonds; ++q) {
+        long long a = p->bonds[2 * q], c = p->bonds[2 * q + 1];
+        if (a < 0 || c < 0 || a >= h->N || c >= h->N || a == c) { delete h; return MD_ERR_ARG; }
+        int ra = 0, rb = 0;
+        while (h->offsets[ra + 1] <= a) ++ra;
+        while (h->offsets[rb + 1] <= c) ++rb;
+        if (ra != rb) { delete h; return MD_ERR_ARG; }
+    }
+
+    // list capacity: 1.5x the ideal-gas count in the list sphere at the
+    // densest replica, plus a margin (grown on overflow by md_build_neighbors)
+    int K = p->list_capacity;
+    h->auto_capacity = (K == 0);
+    if (K == 0) {
+        double kmax = 0;
+        for (auto &R : h->reps) {
+            double V = R.L[0] * R.L[1] * R.L[2];
+            double rl = std::sqrt(R.rl2);
+            kmax = std::fmax(kmax, 1.5 * (double)R.n / V * 4.18879020478639 * rl * rl * rl);
+        }
+        K = (int)round_up((long long)std::ceil(kmax) + 32, 32);
+    }
+
+    Bufs &b = h->b;
+    b.S = h->S;
+    b.N = h->N;
+    b.C = h->C;
+    b.nrep = nrep;
+    b.nblk = h->nblk;
+    b.dt = p->dt;
+    b.mass = p->mass;
+    b.half_dt_over_m = 0.5 * p->dt / p->mass;
+    b.gamma = p->langevin_gamma;
+    b.kT = p->kT;
+    b.langevin = p->langevin_gamma > 0 ? 1 : 0;
+    b.noise_amp = b.langevin ? std::sqrt(24.0 * p->langevin_gamma * p->kT * p->mass / p->dt) : 0.0;
+    b.seed = p->seed;
+    b.fene_K = p->fene_K;
+    b.fene_R02 = p->fene_R0 * p->fene_R0;
+    b.fene_K_f = (float)p->fene_K;
+    b.fene_R02_f = (float)(p->fene_R0 * p->fene_R0);
+
+    bool ok = true;
+    for (int q = 0; q < 2; ++q) {
+        ok &= (b.x[q] = dalloc<double>(h, 3 * h->S)) != nullptr;
+        ok &= (b.v[q] = dalloc<double>(h, 3 * h->S)) != nullptr;
+        ok &= (b.pos[q] = dalloc<uint4>(h, h->S)) != nullptr;
+    }
+    ok &= (b.F = dalloc<double>(h, 3 * h->S)) != nullptr;
+    ok &= (b.xref = dalloc<uint4>(h, h->S)) != nullptr;
+    ok &= (b.slot_of_id = dalloc<int>(h, h->N)) != nullptr;
+    ok &= (b.cellid = dalloc<int>(h, h->S)) != nullptr;
+    ok &= (b.cell_count = dalloc<int>(h, h->C)) != nullptr;
+    ok &= (b.cell_start = dalloc<int>(h, h->C)) != nullptr;
+    ok &= (b.cell_end = dalloc<int>(h, h->C)) != nullptr;
+    ok &= (b.bucket = dalloc<int>(h, h->S)) != nullptr;
+    ok &= (b.nn = dalloc<int>(h, h->S)) != nullptr;
+    ok &= (b.partial = dalloc<double>(h, 4 * (size_t)h->nblk)) != nullptr;
+    ok &= (b.ctl = dalloc<Ctl>(h, 1)) != nullptr;
+    ok &= (h->stage = dalloc<double>(h, 6 * h->N)) != nullptr;
+    ok &= (h->d_count = dalloc<unsigned long long>(h, 1)) != nullptr;
+    Replica *drep = dalloc<Replica>(h, nrep);
+    int *dblk = dalloc<int>(h, h->nblk);
+    ok &= drep && dblk;
+    if (!ok) { md_destroy(h); return MD_ERR_CUDA; }
+    std::vector<int> blk(h->nblk, 0);
+    for (int r = 0; r < nrep; ++r)
+        for (int q = h->reps[r].blk_begin; q < h->reps[r].blk_end; ++q) blk[q] = r;
+    ok &= cudaMemcpy(drep, h->reps.data(), sizeof(Replica) * nrep, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(dblk, blk.data(), sizeof(int) * h->nblk, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemset(b.cell_count, 0, sizeof(int) * h->C) == cudaSuccess;
+    ok &= cudaMemset(b.ctl, 0, sizeof(Ctl)) == cudaSuccess;
+    b.rep = drep;
+    b.blk_rep = dblk;
+
+    // FENE bonds as a per-particle adjacency (both directions)
+    if (p->n_bonds > 0) {
+        std::vector<int> deg(h->N + 1, 0);
+        for (int64_t q = 0; q < p->n_bonds; ++q) {
+            long long a = p->bonds[2 * q], c = p->bonds[2 * q + 1];
+            deg[a + 1]++;
+            deg[c + 1]++;
+        }
+        for (long long q = 0; q < h->N; ++q) deg[q + 1] += deg[q];
+        std::vector<int> partner(2 * p->n_bonds);
+        std::vector<int> fill(deg.begin(), deg.end() - 1);
+        for (int64_t q = 0; q < p->n_bonds; ++q) {
+            int a = p->bonds[2 * q], c = p->bonds[2 * q + 1];
+            partner[fill[a]++] = c;
+            partner[fill[c]++] = a;
+        }
+        int *doff = dalloc<int>(h, h->N + 1);
+        int *dpart = dalloc<int>(h, partner.size());
+        if (!doff || !dpart) { md_destroy(h); return MD_ERR_CUDA; }
+        ok &= cudaMemcpy(doff, deg.data(), sizeof(int) * (h->N + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+        ok &= cudaMemcpy(dpart, partner.data(), sizeof(int) * partner.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        b.bond_off = doff;
+        b.bond_partner = dpart;
+        b.has_bonds = 1;
+    }
+    if (!ok) { md_destroy(h); return MD_ERR_CUDA; }
+    if (alloc_list(h, K) != MD_OK) { md_destroy(h); return MD_ERR_CUDA; }
+    *out = h;
+    return MD_OK;
+}
+
+void md_destroy(md_handle *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (void *q : h->allocs) cudaFree(q);
+    delete h;
+}
+
+md_status md_set_state(md_handle *h, const double *x, const double *v, void *stream)
+{
+    if (!h || !x || !v) return fail(h, MD_ERR_ARG, "md_set_state: null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+    double *xs = h->stage, *vs = h->stage + 3 * h->N;
+    if (!cuda_ok(h, cudaMemcpyAsync(xs, x, bytes, cudaMemcpyDefault, st), "copy positions") ||
+        !cuda_ok(h, cudaMemcpyAsync(vs, v, bytes, cudaMemcpyDefault, st), "copy velocities") ||
+        !cuda_ok(h, cudaMemsetAsync(h->b.cell_count, 0, sizeof(int) * h->C, st), "clear cells"))
+        return MD_ERR_CUDA;
+    mdk::launch_set_state(h->b, xs, vs, st);
+    if (!cuda_ok(h, cudaGetLastError(), "set_state launch")) return MD_ERR_CUDA;
+    h->state_set = true;
+    h->F_valid = false;
+    return MD_OK;
+}
+
+md_status md_get_state(md_handle *h, double *x, double *v, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_get_state before md_set_state");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *xs = h->stage, *vs = h->stage + 3 * h->N;
+    mdk::launch_get_state(h->b, x ? xs : nullptr, v ? vs : nullptr, st);
+    const size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+    if (x && !cuda_ok(h, cudaMemcpyAsync(x, xs, bytes, cudaMemcpyDefault, st), "copy positions out"))
+        return MD_ERR_CUDA;
+    if (v && !cuda_ok(h, cudaMemcpyAsync(v, vs, bytes, cudaMemcpyDefault, st), "copy velocities out"))
+        return MD_ERR_CUDA;
+    return sync_and_check(h, st);
+}
+
+md_status md_build_neighbors(md_handle *h, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_build_neighbors before md_set_state");
+    cudaStream_t st = (cudaStream_t)stream;
+    mdk::launch_set_rebuild(h->b, st);
+    mdk::launch_rebuild_chain(h->b, st);
+    h->F_valid = false;
+    if (!cuda_ok(h, cudaGetLastError(), "rebuild launch")) return MD_ERR_CUDA;
+    if (!h->auto_capacity) return MD_OK;
+    // automatic capacity: check the build and grow the list if it overflowed
+    Ctl c;
+    if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
+    if (read_ctl(h, &c) != MD_OK) return MD_ERR_CUDA;
+    if ((c.err & mdk::kErrList) && c.err == mdk::kErrList) {
+        int K = (int)round_up((long long)(c.max_nn * 1.25) + 32, 32);
+        if (alloc_list(h, K) != MD_OK) return MD_ERR_CUDA;
+        int zero = 0;
+        if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
+            return MD_ERR_CUDA;
+        // the overflowing build still sorted the state and counted every list;
+        // only the entries beyond the old capacity were dropped: build again
+        mdk::launch_set_rebuild(h->b, st);
+        mdk::launch_rebuild_chain(h->b, st);
+        return sync_and_check(h, st);
+    }
+    return status_of(h, c.err);
+}
+
+md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_compute_forces before md_set_state");
+    cudaStream_t st = (cudaStream_t)stream;
+    mdk::launch_rebuild_chain(h->b, st);
+    h->F_valid = false;
+    Bufs b = h->b;
+    double *fs = h->stage;   // 3 N
+    double *th = nullptr;
+    if (euw_out) {
+        if (ensure_thermo(h, 3LL * h->b.nrep) != MD_OK) return MD_ERR_CUDA;
+        th = h->thermo_stage;
+    }
+    b.fout = f_out ? fs : nullptr;
+    b.thermo = euw_out ? th : nullptr;
+    mdk::launch_force(b, h->precision, mdk::kModeOut, euw_out != nullptr, st);
+    if (!cuda_ok(h, cudaGetLastError(), "force launch")) return MD_ERR_CUDA;
+    if (f_out && !cuda_ok(h, cudaMemcpyAsync(f_out, fs, sizeof(double) * 3 * h->N, cudaMemcpyDefault, st),
+                          "copy forces out"))
+        return MD_ERR_CUDA;
+    if (euw_out && !cuda_ok(h, cudaMemcpyAsync(euw_out, th, sizeof(double) * 3 * h->b.nrep, cudaMemcpyDefault, st),
+                            "copy energies out"))
+        return MD_ERR_CUDA;
+    return MD_OK;
+}
+
+md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream)
+{
+    if (!h || nsteps < 0 || thermo_every < 0 || (thermo_every > 0 && !thermo_out))
+        return fail(h, MD_ERR_ARG, "md_step: bad arguments");
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_step before md_set_state");
+    if (nsteps == 0) return MD_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nrep = h->b.nrep;
+    const long long nrec = thermo_every > 0 ? nsteps / thermo_every : 0;
+    if (nrec > 0 && ensure_thermo(h, nrec * 3 * nrep) != MD_OK) return MD_ERR_CUDA;
+    Bufs b = h->b;
+    if (!h->F_valid) {
+        mdk::launch_rebuild_chain(b, st);
+        mdk::launch_force(b, h->precision, mdk::kModeStore, false, st);
+    }
+    mdk::launch_kick_drift(b, st);
+    for (int t = 1; t <= nsteps; ++t) {
+        const bool rec = thermo_every > 0 && (t % thermo_every) == 0;
+        b.thermo = rec ? h->thermo_stage + (long long)(t / thermo_every - 1) * 3 * nrep : nullptr;
+        mdk::launch_rebuild_chain(b, st);
+        mdk::launch_force(b, h->precision, t < nsteps ? mdk::kModeFused : mdk::kModeFinal, rec, st);
+    }
+    if (!cuda_ok(h, cudaGetLastError(), "step launch")) return MD_ERR_CUDA;
+    h->F_valid = true;
+    if (nrec > 0 &&
+        !cuda_ok(h, cudaMemcpyAsync(thermo_out, h->thermo_stage, sizeof(double) * nrec * 3 * nrep, cudaMemcpyDefault, st),
+                 "copy thermo out"))
+        return MD_ERR_CUDA;
+    return MD_OK;
+}
+
+md_status md_export_pairs(md_handle *h, int32_t *pairs_out, int64_t capacity, int64_t *n_out, void *stream)
+{
+    if (!h || !n_out || capacity < 0 || (capacity > 0 && !pairs_out)) return fail(h, MD_ERR_ARG, "md_export_pairs: bad arguments");
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_export_pairs before md_set_state");
+    cudaStream_t st = (cudaStream_t)stream;
+    md_status s = sync_and_check(h, st);
+    if (s != MD_OK) return s;
+    int *tmp = nullptr;
+    if (capacity > 0 && !cuda_ok(h, cudaMalloc(&tmp, sizeof(int) * 2 * (size_t)capacity), "pair buffer"))
+        return MD_ERR_CUDA;
+    cudaMemsetAsync(h->d_count, 0, sizeof(unsigned long long), st);
+    mdk::launch_export_pairs(h->b, tmp, capacity, h->d_count, st);
+    unsigned long long cnt = 0;
+    bool ok = cuda_ok(h, cudaMemcpyAsync(&cnt, h->d_count, sizeof(cnt), cudaMemcpyDeviceToHost, st), "pair count") &&
+              cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize");
+    if (ok && capacity > 0) {
+        long long m = (long long)cnt < capacity ? (long long)cnt : capacity;
+        ok = cuda_ok(h, cudaMemcpy(pairs_out, tmp, sizeof(int) * 2 * (size_t)m, cudaMemcpyDefault), "copy pairs out");
+    }
+    if (tmp) cudaFree(tmp);
+    if (!ok) return MD_ERR_CUDA;
+    *n_out = (int64_t)cnt;
+    return MD_OK;
+}
+
+md_status md_sync(md_handle *h, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    return sync_and_check(h, (cudaStream_t)stream);
+}
+
+md_status md_get_stats(md_handle *h, md_stats *out)
+{
+    if (!h || !out) return MD_ERR_ARG;
+    if (!cuda_ok(h, cudaDeviceSynchronize(), "device synchronize")) return MD_ERR_CUDA;
+    Ctl c;
+    md_status s = read_ctl(h, &c);
+    if (s != MD_OK) return s;
+    std::memset(out, 0, sizeof(*out));
+    out->steps = c.step;
+    out->rebuilds = c.rebuilds;
+    out->list_entries = c.list_entries;
+    out->max_list_len = c.max_nn;
+    out->list_capacity = h->K;
+    out->max_cell_occupancy = c.max_occ;
+    out->error_word = c.err;
+    for (int k = 0; k < 3; ++k) out->ncell[k] = h->reps[0].ncell[k];
+    out->n_replicas = h->b.nrep;
+    out->n_particles = h->N;
+    return status_of(h, c.err);
+}
+
+const char *md_last_error(const md_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+}  // extern "C"

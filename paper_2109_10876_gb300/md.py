@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in include/md.h (same function names).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library lib/libmd_gb300.so.  Arrays may be torch tensors (CUDA or CPU) or
+numpy arrays; their data pointers are passed straight through, so they must
+be contiguous float64 (positions, velocities, forces) in the (3, N)
+component-major layout.  Streams are torch.cuda.Stream objects, raw
+cudaStream_t integers, or None for the current torch stream.
+
+Importing this module loads the library and raises if it is missing: there
+is no fallback implementation.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmd_gb300.so")
+
+MD_OK = 0
+MD_ERR_ARG = -1
+MD_ERR_CUDA = -2
+MD_ERR_LIST_OVERFLOW = -3
+MD_ERR_NONFINITE = -4
+MD_ERR_BOND_BROKEN = -5
+MD_ERR_FIXED_OVERFLOW = -6
+MD_ERR_TIMEOUT = -7
+MD_ERR_BOX_TOO_SMALL = -8
+STATUS_NAMES = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_CUDA", -3: "MD_ERR_LIST_OVERFLOW",
+                -4: "MD_ERR_NONFINITE", -5: "MD_ERR_BOND_BROKEN", -6: "MD_ERR_FIXED_OVERFLOW",
+                -7: "MD_ERR_TIMEOUT", -8: "MD_ERR_BOX_TOO_SMALL"}
+MD_LJ, MD_WCA = 0, 1
+MD_FP64, MD_FP32_FIXED = 0, 1
+
+
+class md_params(C.Structure):
+    _fields_ = [
+        ("n_replicas", C.c_int32),
+        ("replica_offsets", C.POINTER(C.c_int64)),
+        ("box", C.POINTER(C.c_double)),
+        ("eps", C.POINTER(C.c_double)),
+        ("sigma", C.POINTER(C.c_double)),
+        ("rc_over_sigma", C.c_double),
+        ("skin", C.c_double),
+        ("dt", C.c_double),
+        ("mass", C.c_double),
+        ("potential", C.c_int32),
+        ("precision", C.c_int32),
+        ("langevin_gamma", C.c_double),
+        ("kT", C.c_double),
+        ("seed", C.c_uint64),
+        ("fene_K", C.c_double),
+        ("fene_R0", C.c_double),
+        ("n_bonds", C.c_int64),
+        ("bonds", C.POINTER(C.c_int32)),
+        ("list_capacity", C.c_int32),
+        ("reserved0", C.c_int32),
+    ]
+
+
+class md_stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int64),
+        ("rebuilds", C.c_int64),
+        ("list_entries", C.c_int64),
+        ("max_list_len", C.c_int32),
+        ("list_capacity", C.c_int32),
+        ("max_cell_occupancy", C.c_int32),
+        ("error_word", C.c_int32),
+        ("ncell", C.c_int32 * 3),
+        ("n_replicas", C.c_int32),
+        ("n_particles", C.c_int64),
+    ]
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                      "(run paper_2109_10876_gb300/build.py or __graft_entry__.build())")
+_lib = C.CDLL(LIB_PATH)
+_vp = C.c_void_p
+_H = C.c_void_p
+_lib.md_create.restype = C.c_int
+_lib.md_create.argtypes = [C.POINTER(md_params), C.POINTER(_H)]
+_lib.md_destroy.restype = None
+_lib.md_destroy.argtypes = [_H]
+_lib.md_set_state.restype = C.c_int
+_lib.md_set_state.argtypes = [_H, _vp, _vp, _vp]
+_lib.md_get_state.restype = C.c_int
+_lib.md_get_state.argtypes = [_H, _vp, _vp, _vp]
+_lib.md_build_neighbors.restype = C.c_int
+_lib.md_build_neighbors.argtypes = [_H, _vp]
+_lib.md_compute_forces.restype = C.c_int
+_lib.md_compute_forces.argtypes = [_H, _vp, _vp, _vp]
+_lib.md_step.restype = C.c_int
+_lib.md_step.argtypes = [_H, C.c_int32, C.c_int32, _vp, _vp]
+_lib.md_export_pairs.restype = C.c_int
+_lib.md_export_pairs.argtypes = [_H, _vp, C.c_int64, C.POINTER(C.c_int64), _vp]
+_lib.md_sync.restype = C.c_int
+_lib.md_sync.argtypes = [_H, _vp]
+_lib.md_get_stats.restype = C.c_int
+_lib.md_get_stats.argtypes = [_H, C.POINTER(md_stats)]
+_lib.md_last_error.restype = C.c_char_p
+_lib.md_last_error.argtypes = [_H]
+
+
+class MDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a)
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def _check(h, status):
+    if status != MD_OK:
+        msg = _lib.md_last_error(h)
+        raise MDError(status, msg.decode() if msg else "")
+    return status
+
+
+class Handle:
+    """Owns an md_handle*; keeps the host arrays passed to md_create alive."""
+
+    def __init__(self, ptr, keep):
+        self.ptr = ptr
+        self._keep = keep
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "ptr", None):
+            _lib.md_destroy(self.ptr)
+            self.ptr = None
+
+
+def md_create(n_per_replica, box, eps=1.0, sigma=1.0, rc_over_sigma=2.5, skin=0.3, dt=0.005, mass=1.0,
+              potential=MD_LJ, precision=MD_FP32_FIXED, langevin_gamma=0.0, kT=1.0, seed=0,
+              fene_K=30.0, fene_R0=1.5, bonds=None, list_capacity=0):
+    """md_create: n_per_replica is an int or a list of per-replica counts;
+    box is (3,) or (R, 3); eps, sigma scalars or per replica."""
+    sizes = np.atleast_1d(np.asarray(n_per_replica, dtype=np.int64))
+    R = len(sizes)
+    off = np.zeros(R + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    boxa = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (R, 3)))
+    epsa = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (R,)))
+    siga = np.ascontiguousarray(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (R,)))
+    p = md_params()
+    p.n_replicas = R
+    p.replica_offsets = off.ctypes.data_as(C.POINTER(C.c_int64))
+    p.box = boxa.ctypes.data_as(C.POINTER(C.c_double))
+    p.eps = epsa.ctypes.data_as(C.POINTER(C.c_double))
+    p.sigma = siga.ctypes.data_as(C.POINTER(C.c_double))
+    p.rc_over_sigma = rc_over_sigma
+    p.skin = skin
+    p.dt = dt
+    p.mass = mass
+    p.potential = potential
+    p.precision = precision
+    p.langevin_gamma = langevin_gamma
+    p.kT = kT
+    p.seed = seed
+    p.fene_K = fene_K
+    p.fene_R0 = fene_R0
+    bonda = None
+    if bonds is not None and len(bonds):
+        bonda = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+        p.n_bonds = len(bonda)
+        p.bonds = bonda.ctypes.data_as(C.POINTER(C.c_int32))
+    p.list_capacity = list_capacity
+    h = _H()
+    st = _lib.md_create(C.byref(p), C.byref(h))
+    if st != MD_OK:
+        raise MDError(st, "md_create failed")
+    return Handle(h, (off, boxa, epsa, siga, bonda))
+
+
+def md_destroy(h):
+    h.destroy()
+
+
+def md_set_state(h, x, v, stream=None):
+    return _check(h.ptr, _lib.md_set_state(h.ptr, _ptr(x), _ptr(v), _stream(stream)))
+
+
+def md_get_state(h, x, v, stream=None):
+    return _check(h.ptr, _lib.md_get_state(h.ptr, _ptr(x), _ptr(v), _stream(stream)))
+
+
+def md_build_neighbors(h, stream=None):
+    return _check(h.ptr, _lib.md_build_neighbors(h.ptr, _stream(stream)))
+
+
+def md_compute_forces(h, f_out=None, euw_out=None, stream=None):
+    return _check(h.ptr, _lib.md_compute_forces(h.ptr, _ptr(f_out), _ptr(euw_out), _stream(stream)))
+
+
+def md_step(h, nsteps, thermo_every=0, thermo_out=None, stream=None):
+    return _check(h.ptr, _lib.md_step(h.ptr, int(nsteps), int(thermo_every), _ptr(thermo_out), _stream(stream)))
+
+
+def md_export_pairs(h, pairs_out, capacity, stream=None):
+    n = C.c_int64(0)
+    _check(h.ptr, _lib.md_export_pairs(h.ptr, _ptr(pairs_out), int(capacity), C.byref(n), _stream(stream)))
+    return n.value
+
+
+def md_sync(h, stream=None):
+    return _check(h.ptr, _lib.md_sync(h.ptr, _stream(stream)))
+
+
+def md_get_stats(h):
+    s = md_stats()
+    st = _lib.md_get_stats(h.ptr, C.byref(s))
+    _check(h.ptr, st)
+    return {f: (list(getattr(s, f)) if f == "ncell" else getattr(s, f)) for f, _ in md_stats._fields_}
+
+
+def md_last_error(h):
+    m = _lib.md_last_error(h.ptr)
+    return m.decode() if m else ""
+
+
+def export_pairs_sorted(h, stream=None):
+    """All Verlet pairs (i < j) as an (M, 2) int32 array in lexicographic order."""
+    n = md_export_pairs(h, None, 0, stream)
+    out = np.zeros((max(n, 1), 2), dtype=np.int32)
+    m = md_export_pairs(h, out, n, stream)
+    assert m == n
+    out = out[:n]
+    order = np.lexsort((out[:, 1], out[:, 0]))
+    return out[order]
