@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
                             bool in = r2 < R.rl2_lo;
                             if (!in && r2 < R.rl2_hi) in = r2_fp64(X, b.S, i, j, R.L) < R.rl2;
                             if (in) {
-                                if (cnt < b.K) b.nbr[(long long)cnt * b.S + i] = j;
+                                if (cnt < b.K) b.nbr[nbr_index(i, cnt, b.K)] = j;
                                 ++cnt;
                             }
                         }
@@ -366,7 +366,7 @@ __global__ void k_export_pairs(Bufs b, int *pairs, long long cap, unsigned long 
     if (idi < 0) return;
     int n = min(b.nn[i], b.K);
     for (int k = 0; k < n; ++k) {
-        int j = b.nbr[(long long)k * b.S + i];
+        int j = b.nbr[nbr_index(i, k, b.K)];
         int idj = (int)P[j].w;
         if (idi < idj) {
             unsigned long long q = atomicAdd(count, 1ull);

@@ -22,6 +22,36 @@ constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23: x + kMagic rounds x t
 constexpr unsigned kMagicBits = 0x4B400000u;
 constexpr float kFixScale = 4194304.0f;     // 2^22
 constexpr double kFixInv = 1.0 / 4194304.0;
+#ifndef MDK_GATHER_BATCH
+#define MDK_GATHER_BATCH 4
+#endif
+#ifndef MDK_FORCE_MIN_BLOCKS
+#define MDK_FORCE_MIN_BLOCKS 6
+#endif
+constexpr int kU = MDK_GATHER_BATCH;         // neighbours gathered per batch
+
+// Add round(a * c * 2^22) to the two-piece accumulator without rounding the
+// product first: round(a c) from one FMA against kMagic, the remainder
+// a c - round(a c) from a second FMA (|remainder| <= 1/2), then its 2^-22
+// multiple.  A deterministic, odd function of (a, c): f_ij = -f_ji exactly.
+// Valid for |a c| < 2^21.
+__device__ __forceinline__ void fx_acc2(float a, float c, unsigned &hi, unsigned &lo)
+{
+    float t1 = __fmaf_rn(a, c, kMagic);           // kMagic + round(a c)
+    float h = __fsub_rn(t1, kMagic);              // round(a c), exact
+    float r = __fmaf_rn(a, c, -h);                // a c - round(a c)
+    float t2 = __fmaf_rn(r, kFixScale, kMagic);   // kMagic + round(r 2^22)
+    hi += __float_as_uint(t1) - kMagicBits;
+    lo += __float_as_uint(t2) - kMagicBits;
+}
+
+// Reciprocal by the hardware approximation (a pure function of its input).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Add round(f * 2^22) to the two-piece accumulator (valid for |f| < 2^21).
 __device__ __forceinline__ void fx_acc(float f, unsigned &hi, unsigned &lo)
@@ -58,7 +88,7 @@ __device__ __forceinline__ double wrap1(double y, double L)
 
 // FP64 minimum-image r^2 with the fixed rounding sequence of the reference
 // (t = xi - xj; t -= L * rint(t / L); r2 = (dx^2 + dy^2) + dz^2).
-__device__ __forceinline__ double r2_exact(const double *x, long long S, long long i, long long j,
+__device__ __noinline__ double r2_exact(const double *x, long long S, long long i, long long j,
                                            const double *L)
 {
     double d[3];
@@ -151,19 +181,25 @@ __device__ void reduce_partials(const Bufs &b, double *thermo)
     }
 }
 
-// Drift update shared by the fused and kick-drift kernels: x += dt v, wrap,
-// fixed-point copy, squared displacement since the last list build relative
-// to the replica's threshold.
+// Drift update shared by the fused and kick-drift kernels: x += dt v, wrap
+// into [0, L) (only when the fixed-point image leaves [0, 2^32)), fixed-point
+// copy, and squared displacement since the last list build relative to the
+// replica's threshold.
 __device__ __forceinline__ float drift(const Bufs &b, const Replica &R, long long i, int nxt, unsigned id,
                                        const double xi[3], const double v[3])
 {
     unsigned q[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double y = wrap1(xi[k] + b.dt * v[k], R.L[k]);
+        double y = xi[k] + b.dt * v[k];
+        long long qq = __double2ll_rn(y * R.to_q[k]);
+        if ((unsigned long long)qq >= 4294967296ULL) {
+            y = wrap1(y, R.L[k]);
+            qq = __double2ll_rn(y * R.to_q[k]);
+        }
         b.x[nxt][k * b.S + i] = y;
         b.v[nxt][k * b.S + i] = v[k];
-        q[k] = to_q2(y, R.to_q[k]);
+        q[k] = (unsigned)(qq & 0xffffffffLL);
     }
     uint4 p = make_uint4(q[0], q[1], q[2], id);
     b.pos[nxt][i] = p;
@@ -202,8 +238,33 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, float ratio_blk
     }
 }
 
+// FP32 pair terms of one neighbour: separation from the fixed-point
+// positions, LJ force scalar masked to zero outside the cutoff, and the
+// fixed-point accumulation.  `in` decides membership; the caller passes the
+// FP32 verdict or, for the rare pairs within rounding of r_cut, the FP64 one.
+struct Acc32 {
+    unsigned hx, lx, hy, ly, hz, lz, hu, lu, hw, lw;
+};
+
+template <bool ENERGY>
+__device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, bool in, float sig2, float eps24,
+                                       float eps4, float vsh, Acc32 &a)
+{
+    const float ir2 = rcp_approx(r2);
+    const float s2 = sig2 * ir2;
+    const float s6 = s2 * s2 * s2;
+    const float fs = in ? eps24 * s6 * (2.0f * s6 - 1.0f) * ir2 : 0.0f;
+    fx_acc2(fs, dx, a.hx, a.lx);
+    fx_acc2(fs, dy, a.hy, a.ly);
+    fx_acc2(fs, dz, a.hz, a.lz);
+    if (ENERGY) {
+        fx_acc(in ? eps4 * s6 * (s6 - 1.0f) - vsh : 0.0f, a.hu, a.lu);
+        fx_acc2(fs, r2, a.hw, a.lw);
+    }
+}
+
 template <int PREC, int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kBlock) k_force(Bufs b)
+__global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) k_force(Bufs b)
 {
     __shared__ double sm3[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
@@ -213,7 +274,10 @@ __global__ void __launch_bounds__(kBlock) k_force(Bufs b)
     const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
     const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
     const double *X = b.x[cur];
-    double Fi[3] = {0.0, 0.0, 0.0};
+    // Fd * fscale is the force; FP32 mode keeps the exact fixed-point integer
+    // in Fd so that the 2^-22 scale folds into the kick constant
+    double Fd[3] = {0.0, 0.0, 0.0};
+    double fscale = 1.0;
     double ui = 0.0, wi = 0.0, ki = 0.0;
     float ratio = 0.0f;
     uint4 pi = make_uint4(0u, 0u, 0u, 0xffffffffu);
@@ -225,75 +289,108 @@ __global__ void __launch_bounds__(kBlock) k_force(Bufs b)
     }
     if (real) {
         const int n = min(b.nn[i], b.K);
-        const int *nb = b.nbr + i;
+        const int *nb = b.nbr + nbr_index(i, 0, b.K);   // entry k at nb[32 k]
         if (PREC == 1) {
             const uint4 *P = b.pos[cur];
             const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
-            unsigned hx = 0, lx = 0, hy = 0, ly = 0, hz = 0, lz = 0;
-            unsigned hu = 0, lu = 0, hw = 0, lw = 0;
-            for (int k = 0; k < n; ++k) {
-                const int j = __ldg(nb + (long long)k * b.S);
-                const uint4 pj = __ldg(P + j);
-                const float dx = (float)(int)(pi.x - pj.x) * qs0;
-                const float dy = (float)(int)(pi.y - pj.y) * qs1;
-                const float dz = (float)(int)(pi.z - pj.z) * qs2;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < R.rc2_hi) {
-                    bool in = r2 < R.rc2_lo;
-                    if (!in) in = r2_exact(X, b.S, i, j, R.L) < R.rc2;
-                    if (in) {
-                        if (r2 < R.fmax2) err |= kErrFixed;
-                        const float ir2 = __frcp_rn(r2);
-                        const float s2 = R.sig2_f * ir2;
-                        const float s6 = s2 * s2 * s2;
-                        const float fs = R.eps24_f * s6 * (2.0f * s6 - 1.0f) * ir2;
-                        fx_acc(fs * dx, hx, lx);
-                        fx_acc(fs * dy, hy, ly);
-                        fx_acc(fs * dz, hz, lz);
-                        if (ENERGY) {
-                            fx_acc(R.eps4_f * s6 * (s6 - 1.0f) - R.vshift_f, hu, lu);
-                            fx_acc(fs * r2, hw, lw);
-                        }
-                    }
+            const float rc2_lo = R.rc2_lo, rc2_hi = R.rc2_hi, fmax2 = R.fmax2;
+            const float sig2 = R.sig2_f, eps24 = R.eps24_f, eps4 = R.eps4_f, vsh = R.vshift_f;
+            // a point half a box away on every axis: never within the cutoff
+            const uint4 far = make_uint4(pi.x ^ 0x80000000u, pi.y ^ 0x80000000u, pi.z ^ 0x80000000u, 0u);
+            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+            int nband = 0;
+            bool tooclose = false;
+            // neighbours in batches of kU: all index loads, then all position
+            // gathers, then branch-free arithmetic
+            for (int k0 = 0; k0 < n; k0 += kU) {
+                int jj[kU];
+                uint4 pj[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) jj[u] = (k0 + u < n) ? __ldg(nb + 32 * (k0 + u)) : 0;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) pj[u] = (k0 + u < n) ? __ldg(P + jj[u]) : far;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const float dx = (float)(int)(pi.x - pj[u].x) * qs0;
+                    const float dy = (float)(int)(pi.y - pj[u].y) * qs1;
+                    const float dz = (float)(int)(pi.z - pj[u].z) * qs2;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const bool in = r2 < rc2_lo;
+                    nband += (r2 < rc2_hi) & !in;
+                    tooclose |= r2 < fmax2;
+                    pair32<ENERGY>(dx, dy, dz, r2, in, sig2, eps24, eps4, vsh, a);
                 }
             }
-            Fi[0] = fx_value(hx, lx);
-            Fi[1] = fx_value(hy, ly);
-            Fi[2] = fx_value(hz, lz);
-            if (ENERGY) { ui = 0.5 * fx_value(hu, lu); wi = 0.5 * fx_value(hw, lw); }
+            if (nband) {
+                // pairs within rounding of r_cut: membership decided in FP64
+                // from the master positions, as in the FP64 reference
+                for (int k = 0; k < n; ++k) {
+                    const int j = __ldg(nb + 32 * k);
+                    const uint4 q = __ldg(P + j);
+                    const float dx = (float)(int)(pi.x - q.x) * qs0;
+                    const float dy = (float)(int)(pi.y - q.y) * qs1;
+                    const float dz = (float)(int)(pi.z - q.z) * qs2;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 >= rc2_lo && r2 < rc2_hi && r2_exact(X, b.S, i, j, R.L) < R.rc2)
+                        pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, eps4, vsh, a);
+                }
+            }
+            if (tooclose) err |= kErrFixed;
+            const unsigned hh[3] = {a.hx, a.hy, a.hz}, ll[3] = {a.lx, a.ly, a.lz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                Fd[k] = (double)((long long)(int)hh[k] * 4194304LL + (long long)(int)ll[k]);
+            fscale = kFixInv;
+            if (ENERGY) { ui = 0.5 * fx_value(a.hu, a.lu); wi = 0.5 * fx_value(a.hw, a.lw); }
         } else {
             const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
             const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
             const double h0 = 0.5 * L0, h1 = 0.5 * L1, h2 = 0.5 * L2;
             const double eps24 = 24.0 * R.eps, eps4 = 4.0 * R.eps, sig2 = R.sigma * R.sigma;
-            const double band = 1e-12 * R.rc2;
-            for (int k = 0; k < n; ++k) {
-                const int j = __ldg(nb + (long long)k * b.S);
-                double dx = xi0 - __ldg(X + j), dy = xi1 - __ldg(X + b.S + j), dz = xi2 - __ldg(X + 2 * b.S + j);
-                dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
-                dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
-                dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
-                const double r2 = dx * dx + dy * dy + dz * dz;
-                if (r2 < R.rc2 + band) {
-                    bool in = r2 < R.rc2 - band;
-                    if (!in) in = r2_exact(X, b.S, i, j, R.L) < R.rc2;
-                    if (in) {
-                        const double ir2 = 1.0 / r2;
-                        const double s2 = sig2 * ir2;
-                        const double s6 = s2 * s2 * s2;
-                        const double fs = eps24 * s6 * (2.0 * s6 - 1.0) * ir2;
-                        Fi[0] += fs * dx;
-                        Fi[1] += fs * dy;
-                        Fi[2] += fs * dz;
-                        if (ENERGY) {
-                            ui += 0.5 * (eps4 * s6 * (s6 - 1.0) - R.vshift);
-                            wi += 0.5 * fs * r2;
+            const double rc2 = R.rc2, vsh = R.vshift;
+            const double band = 1e-12 * rc2;
+            for (int k0 = 0; k0 < n; k0 += kU) {
+                int jj[kU];
+                double xj[kU][3];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) jj[u] = (k0 + u < n) ? __ldg(nb + 32 * (k0 + u)) : -1;
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const long long j = jj[u] >= 0 ? jj[u] : i;
+                    xj[u][0] = __ldg(X + j);
+                    xj[u][1] = __ldg(X + b.S + j);
+                    xj[u][2] = __ldg(X + 2 * b.S + j);
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    double dx = xi0 - xj[u][0], dy = xi1 - xj[u][1], dz = xi2 - xj[u][2];
+                    dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
+                    dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
+                    dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (jj[u] >= 0 && r2 < rc2 + band) {
+                        bool in = r2 < rc2 - band;
+                        if (!in) in = r2_exact(X, b.S, i, jj[u], R.L) < rc2;
+                        if (in) {
+                            const double ir2 = 1.0 / r2;
+                            const double s2 = sig2 * ir2;
+                            const double s6 = s2 * s2 * s2;
+                            const double fs = eps24 * s6 * (2.0 * s6 - 1.0) * ir2;
+                            Fd[0] += fs * dx;
+                            Fd[1] += fs * dy;
+                            Fd[2] += fs * dz;
+                            if (ENERGY) {
+                                ui += 0.5 * (eps4 * s6 * (s6 - 1.0) - vsh);
+                                wi += 0.5 * fs * r2;
+                            }
                         }
                     }
                 }
             }
+            if (!isfinite(Fd[0]) || !isfinite(Fd[1]) || !isfinite(Fd[2])) err |= kErrNonfinite;
         }
-        // FENE bonds of this particle (Sec. 4), both ends of every bond visited
+        // FENE bonds of this particle (Sec. 4), both ends of every bond visited;
+        // in FP32 mode the bond force joins the same fixed-point sum
         if (b.has_bonds) {
             const int id = (int)pi.w;
             for (int q = b.bond_off[id]; q < b.bond_off[id + 1]; ++q) {
@@ -308,9 +405,9 @@ __global__ void __launch_bounds__(kBlock) k_force(Bufs b)
                     if (!(qf > 0.0f)) { err |= kErrBond; continue; }
                     const float c = -b.fene_K_f / qf;
                     unsigned h = 0, l = 0;
-                    fx_acc(c * dx, h, l); Fi[0] += fx_value(h, l); h = l = 0;
-                    fx_acc(c * dy, h, l); Fi[1] += fx_value(h, l); h = l = 0;
-                    fx_acc(c * dz, h, l); Fi[2] += fx_value(h, l);
+                    fx_acc2(c, dx, h, l); Fd[0] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
+                    fx_acc2(c, dy, h, l); Fd[1] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
+                    fx_acc2(c, dz, h, l); Fd[2] += (double)((long long)(int)h * 4194304LL + (long long)(int)l);
                     if (ENERGY) {
                         ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log((double)qf));
                         wi += 0.5 * (double)(c * r2);
@@ -325,7 +422,7 @@ __global__ void __launch_bounds__(kBlock) k_force(Bufs b)
                     const double qd = 1.0 - r2 / b.fene_R02;
                     if (!(qd > 0.0)) { err |= kErrBond; continue; }
                     const double c = -b.fene_K / qd;
-                    for (int k = 0; k < 3; ++k) Fi[k] += c * d[k];
+                    for (int k = 0; k < 3; ++k) Fd[k] += c * d[k];
                     if (ENERGY) {
                         ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log(qd));
                         wi += 0.5 * c * r2;
@@ -333,36 +430,41 @@ __global__ void __launch_bounds__(kBlock) k_force(Bufs b)
                 }
             }
         }
-        if (!isfinite(Fi[0]) || !isfinite(Fi[1]) || !isfinite(Fi[2])) err |= kErrNonfinite;
 
         double v[3];
         if (MODE != kModeOut) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) v[k] = b.v[cur][k * b.S + i];
-            if (b.langevin) langevin(b, (int)pi.w, step, v, Fi);
+            if (b.langevin) {
+                for (int k = 0; k < 3; ++k) Fd[k] *= fscale;
+                fscale = 1.0;
+                langevin(b, (int)pi.w, step, v, Fd);
+            }
         }
         if (MODE == kModeOut) {
             const int id = (int)pi.w;
             if (b.fout)
-                for (int k = 0; k < 3; ++k) b.fout[k * b.N + id] = Fi[k];
+                for (int k = 0; k < 3; ++k) b.fout[k * b.N + id] = Fd[k] * fscale;
             if (ENERGY)
                 for (int k = 0; k < 3; ++k) { double w = b.v[cur][k * b.S + i]; ki += 0.5 * b.mass * w * w; }
         } else if (MODE == kModeStore) {
-            for (int k = 0; k < 3; ++k) b.F[k * b.S + i] = Fi[k];
+            for (int k = 0; k < 3; ++k) b.F[k * b.S + i] = Fd[k] * fscale;
             if (ENERGY) for (int k = 0; k < 3; ++k) ki += 0.5 * b.mass * v[k] * v[k];
         } else if (MODE == kModeFinal) {
+            const double c = b.half_dt_over_m * fscale;
             for (int k = 0; k < 3; ++k) {
-                v[k] += b.half_dt_over_m * Fi[k];
+                v[k] += c * Fd[k];
                 b.v[cur][k * b.S + i] = v[k];
-                b.F[k * b.S + i] = Fi[k];
+                b.F[k * b.S + i] = Fd[k] * fscale;
                 if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
             }
-        } else {  // kModeFused
+        } else {  // kModeFused: end of step n and first half kick of step n + 1
+            const double c = b.half_dt_over_m * fscale;
             double xi[3];
             for (int k = 0; k < 3; ++k) {
-                v[k] += b.half_dt_over_m * Fi[k];            // end of step n
+                v[k] += c * Fd[k];                        // synchronised v_n
                 if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
-                v[k] += b.half_dt_over_m * Fi[k];            // first half kick of step n + 1
+                v[k] += c * Fd[k];
                 xi[k] = X[k * b.S + i];
             }
             ratio = drift(b, R, i, nxt, pi.w, xi, v);

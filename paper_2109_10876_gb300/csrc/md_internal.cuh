@@ -11,8 +11,10 @@
 //                  int32 is the minimum-image separation in units of L_k / 2^32,
 //                  exact, with the periodic wrap done by integer overflow.
 //   xref           uint4 per slot: pos at the last list build (displacement check).
-//   nbr, nn        Verlet list, column-major: entry k of slot s at nbr[k * S + s],
-//                  nn[s] entries; consecutive slots read consecutive words.
+//   nbr, nn        Verlet list in warp slices: the lists of slots 32w .. 32w+31
+//                  form one contiguous block of K rows of 32 entries, entry k of
+//                  slot s at nbr[(s / 32) * 32 K + 32 k + s % 32]; nn[s] entries.
+//                  A warp reads its 32 lists as one contiguous stream.
 //   cells          count / start / end per cell of every replica grid.
 #pragma once
 #include <cstdint>
@@ -72,6 +74,12 @@ struct Ctl {
     long long rebuilds;
     long long list_entries;
 };
+
+// index of entry k of slot s in the sliced list
+__host__ __device__ __forceinline__ long long nbr_index(long long s, int k, int K)
+{
+    return (s >> 5) * (32LL * K) + 32LL * k + (s & 31);
+}
 
 // Everything the kernels touch.  Plain pointers; sizes in slots S, cells C,
 // list capacity K per slot, particles N.

@@ -147,14 +147,20 @@ def test_trajectory_fp64_100_steps(md):
 
 
 def test_trajectory_fp32_fixed(md):
-    """Same run in FP32 / fixed point: the trajectory stays within FP32-level
-    distance of the FP64 oracle and total momentum stays zero."""
+    """Same run in FP32 / fixed point.  Per-step force errors of ~1e-6
+    relative grow along the chaotic trajectory: after 10 steps the positions
+    agree to 1e-6, after 100 steps (t = 0.5) to 1e-4; total momentum stays
+    zero and the energy agrees to 1e-5."""
     x, v, box = inputs.lj_fluid(10, T=0.72, seed=1)
     n = len(x)
     h = make(md, x, v, box, 1, dt=0.005)
+    x10, _ = run_gpu(md, h, n, 10)
+    xo10, _, _ = oracle.vv_run(oracle.System(n, box, rc=RC, dt=0.005), x, v, 10)
+    assert np.max(np.abs(min_image_diff(x10, xo10, box))) < 1e-6
+    h = make(md, x, v, box, 1, dt=0.005)
     xg, vg, th = run_gpu(md, h, n, 100, thermo_every=100)
     xo, vo, Fo, tho = oracle.vv_run(oracle.System(n, box, rc=RC, dt=0.005), x, v, 100, thermo=True)
-    assert np.max(np.abs(min_image_diff(xg, xo, box))) < 1e-5
+    assert np.max(np.abs(min_image_diff(xg, xo, box))) < 1e-4
     assert np.max(np.abs(vg.sum(axis=0))) < 1e-9
     assert th[-1, 0] == pytest.approx(tho[-1, 0], rel=1e-5)
 
@@ -189,7 +195,7 @@ def test_automatic_capacity_grows(md):
     estimate; md_build_neighbors grows the list and the pair set is exact."""
     box = np.array([30.0, 30.0, 30.0])
     x = np.concatenate([inputs.random_gas(400, box, seed=15),
-                        5.0 + inputs.random_gas(600, np.array([4.5, 4.5, 4.5]), seed=16, rmin=0.8)])
+                        5.0 + inputs.random_gas(700, np.array([9.5, 9.5, 9.5]), seed=16, rmin=0.8)])
     v = np.zeros_like(x)
     h = make(md, x, v, box, 1)
     got = md.export_pairs_sorted(h)
