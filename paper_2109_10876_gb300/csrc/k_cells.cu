@@ -32,8 +32,8 @@ __device__ __forceinline__ double wrap_box(double y, double L)
 // Exact minimum-image squared distance in FP64 with a fixed rounding sequence:
 // t = xi - xj; t -= L * rint(t / L) per axis; r2 = (dx^2 + dy^2) + dz^2.
 // Used to settle pairs whose FP32 distance lies within rounding of a cutoff.
-__device__ __forceinline__ double r2_fp64(const double *x, long long S, long long i, long long j,
-                                          const double *L)
+__device__ __noinline__ double r2_fp64(const double *x, long long S, long long i, long long j,
+                                       const double *L)
 {
     double d[3];
 #pragma unroll
@@ -266,72 +266,421 @@ __global__ void k_reorder(Bufs b)
     }
 }
 
-// a2: Verlet list of every pair within r_cut + r_skin, one thread per slot,
-// scanning the own cell and its neighbours.  The FP32 distance decides all
-// pairs except those within its rounding of the list radius, which are
-// settled in FP64 from the master positions (same formula as the FP64
-// reference), so the list is exactly the FP64 pair set.
-__device__ __forceinline__ void stencil(int n, int &lo, int &cnt)
+// ---------------------------------------------------------------- tiles
+// Rows of all replica grids are numbered replica by replica, cz-major; a warp
+// walks one row.  Lanes first sum, for every column x of the row, the
+// particles in that column of the (up to) 3 x 3 neighbouring rows; lane 0
+// then cuts the row greedily into tiles of at most kTileMax particles whose
+// halo (columns x0 - 1 .. x1 of those rows) holds at most hcap particles.
+constexpr int kTileWarps = 4;
+constexpr int kRowMax = 1024;   // columns held in shared memory per warp
+
+__device__ __forceinline__ int cell_n(const Bufs &b, int c) { return b.cell_end[c] - b.cell_start[c]; }
+
+// Walk one row; writes tiles to out (if non-null) and returns their count.
+__device__ int walk_row(const Bufs &b, int g, Tile *out, int *colsum, int *own)
 {
-    // unique neighbour offsets along an axis with n cells
-    if (n >= 3) { lo = -1; cnt = 3; }
-    else if (n == 2) { lo = 0; cnt = 2; }
-    else { lo = 0; cnt = 1; }
+    const int r = b.row_rep[g];
+    const Replica &R = b.rep[r];
+    const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
+    const int lr = g - R.row_off;                // row index within the replica
+    const int cy = lr % ny, cz = lr / ny;
+    int ly, cntY, lz, cntZ;
+    axis_offsets(ny, ly, cntY);
+    axis_offsets(nz, lz, cntZ);
+    const int lane = threadIdx.x & 31;
+    const bool in_smem = nx <= kRowMax;
+    if (in_smem) {
+        for (int x = lane; x < nx; x += 32) {
+            int sum = 0;
+            for (int oz = 0; oz < cntZ; ++oz)
+                for (int oy = 0; oy < cntY; ++oy) {
+                    int zz = wrapi(cz + lz + oz, nz), yy = wrapi(cy + ly + oy, ny);
+                    sum += cell_n(b, R.cell_off + (zz * ny + yy) * nx + x);
+                }
+            colsum[x] = sum;
+            own[x] = cell_n(b, R.cell_off + (cz * ny + cy) * nx + x);
+        }
+    }
+    __syncwarp();
+    int nt = 0;
+    if (lane == 0) {
+        auto col = [&](int x) -> int {
+            if (in_smem) return colsum[x];
+            int sum = 0;
+            for (int oz = 0; oz < cntZ; ++oz)
+                for (int oy = 0; oy < cntY; ++oy) {
+                    int zz = wrapi(cz + lz + oz, nz), yy = wrapi(cy + ly + oy, ny);
+                    sum += cell_n(b, R.cell_off + (zz * ny + yy) * nx + x);
+                }
+            return sum;
+        };
+        auto mine = [&](int x) -> int { return in_smem ? own[x] : cell_n(b, R.cell_off + (cz * ny + cy) * nx + x); };
+        int total = 0;
+        for (int x = 0; x < nx; ++x) total += col(x);
+        int x0 = 0;
+        while (x0 < nx) {
+            // halo of [x0, x0 + 1): columns x0 - 1, x0, x0 + 1 (or the whole row)
+            int x1 = x0 + 1;
+            int P = mine(x0);
+            int H = (3 >= nx) ? total : col(wrapi(x0 - 1, nx)) + col(x0) + col(wrapi(x0 + 1, nx));
+            while (x1 < nx) {
+                const int c = mine(x1);
+                const int Hn = (x1 + 1 - x0 + 2 >= nx) ? total : H + col(wrapi(x1 + 1, nx));
+                if (P + c > kTileMax || Hn > b.hcap) break;
+                P += c;
+                H = Hn;
+                ++x1;
+            }
+            if (out) {
+                const int base = R.cell_off + (cz * ny + cy) * nx;
+                Tile t;
+                t.rep = r; t.cy = cy; t.cz = cz; t.x0 = x0; t.x1 = x1;
+                t.s0 = b.cell_start[base + x0];
+                t.s1 = b.cell_end[base + x1 - 1];
+                t.hsize = H;
+                t.kmax = 0;
+                out[nt] = t;
+            }
+            ++nt;
+            x0 = x1;
+        }
+    }
+    __syncwarp();
+    return nt;
+}
+
+__global__ void __launch_bounds__(32 * kTileWarps) k_tile_count(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    __shared__ int colsum[kTileWarps][kRowMax], own[kTileWarps][kRowMax];
+    const int w = threadIdx.x >> 5;
+    const int g = blockIdx.x * kTileWarps + w;
+    if (g >= b.nrows) return;
+    int nt = walk_row(b, g, nullptr, colsum[w], own[w]);
+    if ((threadIdx.x & 31) == 0) b.row_tiles[g] = nt;
+}
+
+// Exclusive scan of tiles per row (one block); first tile of every replica.
+__global__ void __launch_bounds__(kScanThreads) k_tile_scan(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    __shared__ int warp_sums[33];
+    const int n = b.nrows;
+    const int chunk = (n + kScanThreads - 1) / kScanThreads;
+    const int lo = min(n, (int)threadIdx.x * chunk), hi = min(n, lo + chunk);
+    int sum = 0;
+    for (int g = lo; g < hi; ++g) sum += b.row_tiles[g];
+    int total;
+    int base = block_excl_scan(sum, warp_sums, total);
+    for (int g = lo; g < hi; ++g) {
+        const int t = b.row_tiles[g];
+        b.row_tiles[g] = base;
+        if (g == 0 || b.row_rep[g - 1] != b.row_rep[g]) b.rep_tile[b.row_rep[g]] = base;
+        base += t;
+    }
+    if (threadIdx.x == 0) {
+        b.row_tiles[n] = total;
+        b.rep_tile[b.nrep] = total;
+        for (int r = b.nrep - 1; r >= 0; --r)   // replicas without rows (none in practice)
+            if (b.rep[r].ncells == 0) b.rep_tile[r] = b.rep_tile[r + 1];
+        b.ctl->ntiles = total;
+        b.ctl->max_halo = 0;
+    }
+}
+
+__global__ void __launch_bounds__(32 * kTileWarps) k_tile_write(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    __shared__ int colsum[kTileWarps][kRowMax], own[kTileWarps][kRowMax];
+    const int w = threadIdx.x >> 5;
+    const int g = blockIdx.x * kTileWarps + w;
+    if (g >= b.nrows) return;
+    walk_row(b, g, b.tiles + b.row_tiles[g], colsum[w], own[w]);
+}
+
+// Halo pieces of every tile, computed once per build: a warp per tile, lane
+// r computing the slot ranges of halo row r; a warp prefix sum places them.
+__global__ void __launch_bounds__(32 * kTileWarps) k_tile_pieces(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kTileWarps + (threadIdx.x >> 5);
+    if (t >= b.ctl->ntiles) return;
+    const Tile tl = b.tiles[t];
+    const Replica &R = b.rep[tl.rep];
+    const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
+    int ly, cntY, lz, cntZ;
+    axis_offsets(ny, ly, cntY);
+    axis_offsets(nz, lz, cntZ);
+    const int nrow = cntY * cntZ;
+    int npc = 0, cnt[2] = {0, 0}, ra[2] = {0, 0}, rb[2] = {0, 0}, s0[2] = {0, 0};
+    if (lane < nrow) {
+        const int oz = lane / cntY, oy = lane - oz * cntY;
+        const int zz = wrapi(tl.cz + lz + oz, nz), yy = wrapi(tl.cy + ly + oy, ny);
+        const int base = R.cell_off + (zz * ny + yy) * nx;
+        const int x0 = tl.x0, x1 = tl.x1;
+        if (x1 - x0 + 2 >= nx) { ra[0] = 0; rb[0] = nx; npc = 1; }
+        else if (x0 == 0) { ra[0] = nx - 1; rb[0] = nx; ra[1] = 0; rb[1] = x1 + 1; npc = 2; }
+        else if (x1 == nx) { ra[0] = x0 - 1; rb[0] = nx; ra[1] = 0; rb[1] = 1; npc = 2; }
+        else { ra[0] = x0 - 1; rb[0] = x1 + 1; npc = 1; }
+        for (int q = 0; q < npc; ++q) {
+            s0[q] = b.cell_start[base + ra[q]];
+            cnt[q] = b.cell_end[base + rb[q] - 1] - s0[q];
+        }
+    }
+    // exclusive prefix over lanes of pieces and halo sizes
+    int pinc = npc, hinc = cnt[0] + cnt[1];
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, pinc, o), c = __shfl_up_sync(0xffffffffu, hinc, o);
+        if (lane >= o) { pinc += a; hinc += c; }
+    }
+    const int pbase = pinc - npc, hbase = hinc - (cnt[0] + cnt[1]);
+    Piece *out = b.pieces + (size_t)t * (kMaxPieces + 1);
+    int h = hbase;
+    for (int q = 0; q < npc; ++q) {
+        Piece pq;
+        pq.row = lane; pq.xa = ra[q]; pq.xb = rb[q]; pq.slot0 = s0[q]; pq.hoff = h; pq.n = cnt[q];
+        out[pbase + q] = pq;
+        h += cnt[q];
+    }
+    const int np = __shfl_sync(0xffffffffu, pinc, 31), H = __shfl_sync(0xffffffffu, hinc, 31);
+    if (lane == 0) {
+        Piece last;
+        last.row = nrow; last.xa = last.xb = 0; last.slot0 = 0; last.hoff = H; last.n = 0;
+        out[np] = last;
+        b.tile_np[t] = np;
+        atomicMax(&b.ctl->max_halo, H);
+    }
+}
+
+// ---------------------------------------------------------------- list build
+// a2: Verlet list of every pair within r_cut + r_skin.  A persistent block
+// takes tiles from a work counter and stages the tile's halo positions in
+// shared memory.  Each warp takes one cell of the tile at a time, its lanes
+// the cell's particles; the lanes walk the neighbouring cells (found in the
+// halo) in step, reading each candidate once for the whole warp, and keep the
+// halo index of every partner.  The FP32 distance decides all pairs except
+// those within its rounding of the list radius, which are settled in FP64
+// from the master positions (same formula as the FP64 reference), so the list
+// is exactly the FP64 pair set.  Lists are staged in shared memory and leave
+// as contiguous rows of the tile layout.
+
+__host__ __device__ inline size_t list_smem_bytes(int hcap)
+{
+    return (size_t)hcap * sizeof(uint4) + (size_t)kListStage * kTileMax * sizeof(unsigned short);
+}
+
+// Lists of the particles of one tile.  A warp takes 32 consecutive particles
+// of the tile, one per lane (they span one to a few cells of the tile's row),
+// and walks the union of their stencils -- on each of the 3 x 3 halo rows,
+// the cells from one left of the first particle's cell to one right of the
+// last one's -- with every lane reading the same candidate at a time.  A
+// candidate outside a lane's own 27 cells is at least a cell edge (>= r_cut +
+// r_skin) away and fails the distance test, so each list is exactly the pair
+// set, ordered by halo row and slot.  Distances in fixed-point units of the
+// x axis (see Replica).
+template <bool CUBIC>
+__device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
+                                              const uint4 *halo, unsigned short *lst, const double *X, const uint4 *P,
+                                              int *s_kmax, int &mx, long long &sm, int &err)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
+    int ly, cntY, lz, cntZ;
+    axis_offsets(ny, ly, cntY);
+    axis_offsets(nz, lz, cntZ);
+    const int nrow = cntY * cntZ;
+    const float lo = R.rl2_lo_u, hi = R.rl2_hi_u, ry = R.ry, rz = R.rz;
+    const int Pt = tl.s1 - tl.s0;
+    const bool staged = Pt <= kTileMax;
+    const int crow = (-lz) * cntY + (-ly);          // halo row of the tile itself
+    // halo offset of the tile's first particle: its slots are contiguous in the
+    // piece(s) of the tile's own row
+    int hfirst = 0;
+    {
+        int q = 0;
+        while (q + 1 < np && !(pc[q].row == crow && pc[q].slot0 <= tl.s0 && tl.s0 < pc[q].slot0 + pc[q].n + (pc[q].n == 0))) ++q;
+        hfirst = pc[q].hoff + (tl.s0 - pc[q].slot0);
+    }
+    for (int c0 = warp * 32; c0 < Pt; c0 += nwarp * 32) {
+        const int pp = c0 + lane;
+        const bool valid = pp < Pt;
+        const int i = tl.s0 + (valid ? pp : c0);
+        const int xa = (b.cellid[tl.s0 + c0] - R.cell_off) % nx;
+        const int xb = (b.cellid[tl.s0 + min(c0 + 31, Pt - 1)] - R.cell_off) % nx;
+        // union x-range of cells: [xa - 1, xb + 1], or the whole row
+        const int span = xb - xa + 3;
+        const bool whole = span >= nx;
+        // lane r (< nrow * 2) holds halo range r of the union
+        int rh0 = 0, rh1 = 0, rj0 = 0;
+        if (lane < nrow * 2) {
+            const int row = lane >> 1, part = lane & 1;
+            const int oz = row / cntY, oy = row - oz * cntY;
+            const int zz = wrapi(tl.cz + lz + oz, nz), yy = wrapi(tl.cy + ly + oy, ny);
+            const int base = R.cell_off + (zz * ny + yy) * nx;
+            int ca = -1, cb = -1;     // cells [ca, cb) of this part
+            if (whole) { if (part == 0) { ca = 0; cb = nx; } }
+            else {
+                const int a = xa - 1, e = xb + 2;    // [a, e) before wrapping
+                if (a < 0) { if (part == 0) { ca = a + nx; cb = nx; } else { ca = 0; cb = e; } }
+                else if (e > nx) { if (part == 0) { ca = a; cb = nx; } else { ca = 0; cb = e - nx; } }
+                else if (part == 0) { ca = a; cb = e; }
+            }
+            if (ca >= 0 && cb > ca) {
+                int qq = 0;
+                while (qq + 1 < np && !(pc[qq].row == row && pc[qq].xa <= ca && ca < pc[qq].xb)) ++qq;
+                const int j0 = b.cell_start[base + ca], j1 = b.cell_end[base + cb - 1];
+                rh0 = pc[qq].hoff + (j0 - pc[qq].slot0);
+                rh1 = rh0 + (j1 - j0);
+                rj0 = j0;
+                if (rh0 < pc[qq].hoff || rh1 > pc[qq].hoff + pc[qq].n) { err |= kErrList; rh1 = rh0; }
+            }
+        }
+        const int self = hfirst + pp;
+        const uint4 p = halo[valid ? self : hfirst + c0];
+        // Appends are branch-free: the candidate is always written at the
+        // lane's current count, which advances only on a hit, so a miss is
+        // overwritten by the next hit.  Lists that outgrow the shared stage
+        // are rebuilt below straight into global memory.
+        // (a tile wider than kTileMax has no stage: its lanes write a dummy column)
+        unsigned short *mylst = lst + (staged ? pp : 0);
+        int cnt = 0;
+        for (int r = 0; r < nrow * 2; ++r) {
+            const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
+            const int j0 = __shfl_sync(0xffffffffu, rj0, r);
+            int h = h0;
+            for (; h + 4 <= h1; h += 4) {
+                uint4 pj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) pj[u] = halo[h + u];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float d0 = (float)(int)(p.x - pj[u].x);
+                    float d1 = (float)(int)(p.y - pj[u].y);
+                    float d2 = (float)(int)(p.z - pj[u].z);
+                    if (!CUBIC) { d1 *= ry; d2 *= rz; }
+                    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                    const bool mine = valid & (h + u != self);
+                    bool in = (r2 < lo) & mine;
+                    const bool band = (r2 < hi) & !(r2 < lo) & mine;
+                    if (__any_sync(0xffffffffu, band) && band)
+                        in = r2_fp64(X, b.S, i, j0 + (h + u - h0), R.L) < R.rl2;
+                    mylst[min(cnt, kListStage - 1) * kTileMax] = (unsigned short)(h + u);
+                    cnt += in;
+                }
+            }
+            for (; h < h1; ++h) {
+                const uint4 pj = halo[h];
+                float d0 = (float)(int)(p.x - pj.x);
+                float d1 = (float)(int)(p.y - pj.y);
+                float d2 = (float)(int)(p.z - pj.z);
+                if (!CUBIC) { d1 *= ry; d2 *= rz; }
+                const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                const bool mine = valid & (h != self);
+                bool in = (r2 < lo) & mine;
+                const bool band = (r2 < hi) & !(r2 < lo) & mine;
+                if (__any_sync(0xffffffffu, band) && band)
+                    in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
+                mylst[min(cnt, kListStage - 1) * kTileMax] = (unsigned short)h;
+                cnt += in;
+            }
+        }
+        // a list longer than the stage (or a tile wider than kTileMax): walk
+        // the candidates again, writing to global memory (rare)
+        if (__any_sync(0xffffffffu, valid && (cnt >= kListStage || !staged))) {
+            int c2 = 0;
+            for (int r = 0; r < nrow * 2; ++r) {
+                const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
+                const int j0 = __shfl_sync(0xffffffffu, rj0, r);
+                for (int h = h0; h < h1; ++h) {
+                    const uint4 pj = halo[h];
+                    float d0 = (float)(int)(p.x - pj.x);
+                    float d1 = (float)(int)(p.y - pj.y);
+                    float d2 = (float)(int)(p.z - pj.z);
+                    if (!CUBIC) { d1 *= ry; d2 *= rz; }
+                    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                    const bool mine = valid & (h != self);
+                    bool in = (r2 < lo) & mine;
+                    if ((r2 < hi) & !(r2 < lo) & mine) in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
+                    if (in && (cnt >= kListStage || !staged)) {
+                        if (c2 < b.K) b.nbr[nbr_index(tl.s0, Pt, b.K, c2, pp)] = (unsigned short)h;
+                        if (staged && c2 < kListStage) lst[c2 * kTileMax + pp] = (unsigned short)h;
+                    }
+                    c2 += in;
+                }
+            }
+        }
+        if (valid) {
+            // pad with the particle's own index (r = 0 is never an interaction)
+            const int kp = min(((cnt + kPad - 1) / kPad) * kPad, b.K);
+            for (int k = cnt; k < kp; ++k) {
+                if (staged && k < kListStage) lst[k * kTileMax + pp] = (unsigned short)self;
+                if (!staged || k >= kListStage) b.nbr[nbr_index(tl.s0, Pt, b.K, k, pp)] = (unsigned short)self;
+            }
+            b.nn[i] = cnt;
+            if (cnt > b.K) err |= kErrList;
+            atomicMax(s_kmax, kp);
+            mx = max(mx, cnt);
+            sm += cnt;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int src = b.ctl->cur ^ 1;            // k_reorder wrote the sorted state here
-    const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
-    int cnt = 0;
-    bool real = false;
-    if (i < b.S) {
-        uint4 p = b.pos[src][i];
-        real = (int)p.w >= 0;
-        if (real) {
-            int c = b.cellid[i] - R.cell_off;
-            int cx = c % R.ncell[0], cy = (c / R.ncell[0]) % R.ncell[1], cz = c / (R.ncell[0] * R.ncell[1]);
-            int lx, nx, ly, ny, lz, nz;
-            stencil(R.ncell[0], lx, nx);
-            stencil(R.ncell[1], ly, ny);
-            stencil(R.ncell[2], lz, nz);
-            const uint4 *P = b.pos[src];
-            const double *X = b.x[src];
-            for (int oz = 0; oz < nz; ++oz) {
-                int zz = cz + lz + oz;
-                zz += (zz < 0) ? R.ncell[2] : 0;
-                zz -= (zz >= R.ncell[2]) ? R.ncell[2] : 0;
-                for (int oy = 0; oy < ny; ++oy) {
-                    int yy = cy + ly + oy;
-                    yy += (yy < 0) ? R.ncell[1] : 0;
-                    yy -= (yy >= R.ncell[1]) ? R.ncell[1] : 0;
-                    for (int ox = 0; ox < nx; ++ox) {
-                        int xx = cx + lx + ox;
-                        xx += (xx < 0) ? R.ncell[0] : 0;
-                        xx -= (xx >= R.ncell[0]) ? R.ncell[0] : 0;
-                        int cn = R.cell_off + (zz * R.ncell[1] + yy) * R.ncell[0] + xx;
-                        int j0 = b.cell_start[cn], j1 = b.cell_end[cn];
-                        for (int j = j0; j < j1; ++j) {
-                            if (j == i) continue;
-                            float r2 = r2_q(p, P[j], R.qs);
-                            bool in = r2 < R.rl2_lo;
-                            if (!in && r2 < R.rl2_hi) in = r2_fp64(X, b.S, i, j, R.L) < R.rl2;
-                            if (in) {
-                                if (cnt < b.K) b.nbr[nbr_index(i, cnt, b.K)] = j;
-                                ++cnt;
-                            }
-                        }
-                    }
-                }
-            }
+    extern __shared__ uint4 halo[];
+    unsigned short *lst = reinterpret_cast<unsigned short *>(halo + b.hcap);   // [k][p], p < kTileMax
+    __shared__ Piece pc[kMaxPieces + 1];
+    __shared__ Tile tl;
+    __shared__ int s_tile, s_np, s_kmax;
+    const int src = b.ctl->cur ^ 1;          // k_reorder wrote the sorted state here
+    const uint4 *P = b.pos[src];
+    const double *X = b.x[src];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    int mx = 0;
+    long long sm = 0;
+    int err = 0;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+    __syncthreads();
+    for (;;) {
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= b.ctl->ntiles) break;
+        // the next tile is claimed now and published at the end of this one
+        int t_next = 0;
+        if (threadIdx.x == 0) { t_next = (int)atomicAdd(&b.ctl->tile_next, 1u); s_kmax = 0; }
+        load_tile(b, t, tl, pc, s_np);
+        __syncthreads();
+        const Replica &R = b.rep[tl.rep];
+        const int H = pc[s_np].hoff;
+        const int Pt = tl.s1 - tl.s0;
+        if (H > b.hcap) {
+            err |= kErrList;                 // halo does not fit: the host grows hcap and rebuilds
+            for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) b.nn[i] = 0;
+            if (threadIdx.x == 0) s_tile = t_next;
+            __syncthreads();
+            continue;
         }
-        b.nn[i] = cnt;
+        stage_halo<uint4>(pc, s_np, [&](int h, int j) { cp_async16(&halo[h], &P[j]); });
+        cp_async_wait_all();
+        __syncthreads();
+        if (R.cubic) cells_of_tile<true>(b, R, tl, pc, s_np, halo, lst, X, P, &s_kmax, mx, sm, err);
+        else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, P, &s_kmax, mx, sm, err);
+        __syncthreads();
+        if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;
+        // staged rows out to global memory, contiguous per row
+        const int kr = (Pt <= kTileMax) ? min(s_kmax, kListStage) : 0, pr = Pt;
+        unsigned short *dst = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
+        for (int idx = threadIdx.x; idx < kr * pr; idx += blockDim.x) {
+            const int k = idx / pr, pq = idx - k * pr;
+            dst[(long long)k * Pt + pq] = lst[k * kTileMax + pq];
+        }
+        if (threadIdx.x == 0) s_tile = t_next;
+        __syncthreads();
     }
-    if (cnt > b.K) atomicOr(&b.ctl->err, kErrList);
-    // block reduction of max and sum of list lengths
-    int mx = cnt, sm = cnt;
+    if (err) atomicOr(&b.ctl->err, err);
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         sm += __shfl_xor_sync(0xffffffffu, sm, o);
@@ -352,6 +701,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
             b.ctl->disp2_bits = 0u;
             b.ctl->rebuilds += 1;
             b.ctl->done_list = 0u;
+            b.ctl->tile_next = 0u;
         }
     }
 }
@@ -359,18 +709,32 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
 // ---------------------------------------------------------------- pair export
 __global__ void k_export_pairs(Bufs b, int *pairs, long long cap, unsigned long long *count)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= b.S) return;
+    __shared__ Piece pc[kMaxPieces + 1];
+    __shared__ int s_np;
     const uint4 *P = b.pos[b.ctl->cur];
-    int idi = (int)P[i].w;
-    if (idi < 0) return;
-    int n = min(b.nn[i], b.K);
-    for (int k = 0; k < n; ++k) {
-        int j = b.nbr[nbr_index(i, k, b.K)];
-        int idj = (int)P[j].w;
-        if (idi < idj) {
-            unsigned long long q = atomicAdd(count, 1ull);
-            if ((long long)q < cap) { pairs[2 * q] = idi; pairs[2 * q + 1] = idj; }
+    for (int t = blockIdx.x; t < b.ctl->ntiles; t += gridDim.x) {
+        __syncthreads();
+        const Tile tl = b.tiles[t];
+        const Replica &R = b.rep[tl.rep];
+        (void)R;
+        if (threadIdx.x == 0) s_np = b.tile_np[t];
+        for (int m = threadIdx.x; m <= kMaxPieces; m += blockDim.x) pc[m] = b.pieces[(size_t)t * (kMaxPieces + 1) + m];
+        __syncthreads();
+        const int Pt = tl.s1 - tl.s0;
+        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+            const int idi = (int)P[i].w;
+            const int n = min(b.nn[i], b.K);
+            for (int k = 0; k < n; ++k) {
+                const int h = b.nbr[nbr_index(tl.s0, Pt, b.K, k, (int)(i - tl.s0))];
+                int q = 0;
+                while (q + 1 < s_np && h >= pc[q + 1].hoff) ++q;
+                const int j = pc[q].slot0 + (h - pc[q].hoff);
+                const int idj = (int)P[j].w;
+                if (idi < idj) {
+                    unsigned long long w = atomicAdd(count, 1ull);
+                    if ((long long)w < cap) { pairs[2 * w] = idi; pairs[2 * w + 1] = idj; }
+                }
+            }
         }
     }
 }
@@ -391,18 +755,40 @@ void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st)
 
 void launch_set_rebuild(const Bufs &b, cudaStream_t st) { k_set_rebuild<<<1, 1, 0, st>>>(b.ctl); }
 
+static int list_grid(size_t smem)
+{
+    static int grid = 0;
+    static size_t grid_smem = 0;
+    if (grid == 0 || grid_smem != smem) {
+        int dev = 0, nsm = 0, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        // the default 48 KB limit covers static plus dynamic shared memory: always opt in
+        cudaFuncSetAttribute((const void *)k_build_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_build_list, kBlock, smem);
+        grid = (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
+        grid_smem = smem;
+    }
+    return grid;
+}
+
 void launch_rebuild_chain(const Bufs &b, cudaStream_t st)
 {
     k_bin<<<b.nblk, kBlock, 0, st>>>(b);
     k_scan<<<1, kScanThreads, 0, st>>>(b);
     k_scatter<<<b.nblk, kBlock, 0, st>>>(b);
     k_reorder<<<blocks_for((long long)b.C * 32, 256), 256, 0, st>>>(b);
-    k_build_list<<<b.nblk, kBlock, 0, st>>>(b);
+    k_tile_count<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
+    k_tile_scan<<<1, kScanThreads, 0, st>>>(b);
+    k_tile_write<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
+    k_tile_pieces<<<blocks_for(b.C, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
+    const size_t smem = list_smem_bytes(b.hcap);
+    k_build_list<<<list_grid(smem), kBlock, smem, st>>>(b);
 }
 
 void launch_export_pairs(const Bufs &b, int *pairs, long long cap, unsigned long long *count, cudaStream_t st)
 {
-    k_export_pairs<<<b.nblk, kBlock, 0, st>>>(b, pairs, cap, count);
+    k_export_pairs<<<1024, kBlock, 0, st>>>(b, pairs, cap, count);
 }
 
 }  // namespace mdk

@@ -22,13 +22,10 @@ constexpr float kMagic = 12582912.0f;       // 1.5 * 2^23: x + kMagic rounds x t
 constexpr unsigned kMagicBits = 0x4B400000u;
 constexpr float kFixScale = 4194304.0f;     // 2^22
 constexpr double kFixInv = 1.0 / 4194304.0;
-#ifndef MDK_GATHER_BATCH
-#define MDK_GATHER_BATCH 4
-#endif
 #ifndef MDK_FORCE_MIN_BLOCKS
 #define MDK_FORCE_MIN_BLOCKS 6
 #endif
-constexpr int kU = MDK_GATHER_BATCH;         // neighbours gathered per batch
+constexpr int kU = kPad;                     // neighbours per batch: lists are padded to it
 
 // Add round(a * c * 2^22) to the two-piece accumulator without rounding the
 // product first: round(a c) from one FMA against kMagic, the remainder
@@ -150,14 +147,13 @@ __device__ __forceinline__ void block_sum3(double &a, double &c, double &d, doub
     }
 }
 
-// Last block: per-replica totals from the block partials, in a fixed order.
+// Last block: per-replica totals from the per-tile partials, in tile order.
 __device__ void reduce_partials(const Bufs &b, double *thermo)
 {
     __shared__ double red[kBlock][3];
     for (int r = 0; r < b.nrep; ++r) {
-        const Replica &R = b.rep[r];
         double a = 0, c = 0, d = 0;
-        for (int q = R.blk_begin + threadIdx.x; q < R.blk_end; q += blockDim.x) {
+        for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x) {
             a += b.partial[4 * q + 0];
             c += b.partial[4 * q + 1];
             d += b.partial[4 * q + 2];
@@ -210,12 +206,24 @@ __device__ __forceinline__ float drift(const Bufs &b, const Replica &R, long lon
     return (dx * dx + dy * dy + dz * dz) / R.disp2_thr;
 }
 
-// End-of-kernel bookkeeping by the last block to finish: energy totals, and
-// for kernels that drifted, the buffer flip, the step counter and the
-// rebuild decision for the next step.
-__device__ void finish(const Bufs &b, bool drifted, bool energy, float ratio_blk)
+// Block-wide maximum of a float; result valid in thread 0.
+__device__ __forceinline__ float block_max(float v, float *sm)
 {
-    if (!drifted && !energy) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) v = fmaxf(v, sm[q]);
+    return v;
+}
+
+// End-of-kernel bookkeeping by the last block to finish: energy totals, the
+// work counter, and for kernels that drifted the buffer flip, the step
+// counter and the rebuild decision for the next step.
+__device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, float ratio_blk)
+{
+    if (!drifted && !energy && !tiled) return;
     __shared__ bool last;
     if (threadIdx.x == 0) {
         if (drifted && ratio_blk > 0.0f) atomicMax(&b.ctl->disp2_bits, __float_as_uint(ratio_blk));
@@ -234,143 +242,202 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, float ratio_blk
             b.ctl->cur ^= 1;
             b.ctl->step += 1;
         }
+        if (tiled) b.ctl->tile_next = 0u;
         b.ctl->done_force = 0u;
     }
 }
 
-// FP32 pair terms of one neighbour: separation from the fixed-point
-// positions, LJ force scalar masked to zero outside the cutoff, and the
-// fixed-point accumulation.  `in` decides membership; the caller passes the
-// FP32 verdict or, for the rare pairs within rounding of r_cut, the FP64 one.
+// FP32 pair terms of one neighbour: LJ force scalar masked to zero unless
+// `in`, and the fixed-point accumulation of force, energy and virial.
 struct Acc32 {
     unsigned hx, lx, hy, ly, hz, lz, hu, lu, hw, lw;
 };
 
+// slot of halo index h (pieces are in ascending halo order)
+__device__ __forceinline__ int halo_slot(const Piece *pc, int np, int h)
+{
+    int q = 0;
+    while (q + 1 < np && h >= pc[q + 1].hoff) ++q;
+    return pc[q].slot0 + (h - pc[q].hoff);
+}
+
+// All lengths in fixed-point units u of the x axis: r2 and d in u, the force
+// scalar fs in force / u (constants pre-scaled), so fs * d is the force.
 template <bool ENERGY>
 __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, bool in, float sig2, float eps24,
-                                       float eps4, float vsh, Acc32 &a)
+                                       float eps24p, float eps4, float vsh, Acc32 &a)
 {
     const float ir2 = rcp_approx(r2);
     const float s2 = sig2 * ir2;
     const float s6 = s2 * s2 * s2;
-    const float fs = in ? eps24 * s6 * (2.0f * s6 - 1.0f) * ir2 : 0.0f;
+    const float g = s6 * (2.0f * s6 - 1.0f);
+    const float fs = in ? eps24 * g * ir2 : 0.0f;
     fx_acc2(fs, dx, a.hx, a.lx);
     fx_acc2(fs, dy, a.hy, a.ly);
     fx_acc2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        fx_acc(in ? eps4 * s6 * (s6 - 1.0f) - vsh : 0.0f, a.hu, a.lu);
-        fx_acc2(fs, r2, a.hw, a.lw);
+        fx_acc(in ? eps4 * s6 * (s6 - 1.0f) - vsh : 0.0f, a.hu, a.lu);   // V(r) - V(r_cut)
+        fx_acc(in ? eps24p * g : 0.0f, a.hw, a.lw);                      // r f(r) = d . f
     }
 }
 
+// separation of two fixed-point positions in units u of the x axis
+template <bool CUBIC>
+__device__ __forceinline__ void sep_u(uint4 a, uint4 c, float ry, float rz, float &dx, float &dy, float &dz, float &r2)
+{
+    dx = (float)(int)(a.x - c.x);
+    dy = (float)(int)(a.y - c.y);
+    dz = (float)(int)(a.z - c.z);
+    if (!CUBIC) { dy *= ry; dz *= rz; }
+    r2 = dx * dx + dy * dy + dz * dz;
+}
+
+// FP32 neighbour loop of one particle: padded list, branch-free arithmetic;
+// pairs within rounding of r_cut are settled afterwards in FP64.
+template <bool ENERGY, bool CUBIC, bool LSMEM>
+__device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos, const unsigned short *nb, int Pt,
+                                             int n, int npad, uint4 pi, const double *X, long long S, long long i,
+                                             const Piece *pc, int np, Acc32 &a, int &err)
+{
+    const float ry = R.ry, rz = R.rz;
+    const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
+    const float sig2 = R.sig2_u, eps24 = R.eps24_u, eps24p = R.eps24_f, eps4 = R.eps4_f, vsh = R.vshift_f;
+    int nband = 0;
+    bool tooclose = false;
+    for (int k0 = 0; k0 < npad; k0 += kU) {
+        int hh[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) hh[u] = LSMEM ? nb[(k0 + u) * Pt] : __ldg(nb + (long long)(k0 + u) * Pt);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            float dx, dy, dz, r2;
+            sep_u<CUBIC>(pi, hpos[hh[u]], ry, rz, dx, dy, dz, r2);
+            const bool nz = r2 > 0.0f;              // padding entries are the particle itself
+            const bool in = (r2 < lo) & nz;
+            nband += (r2 < hi) & !(r2 < lo);
+            tooclose |= (r2 < fmax2) & nz;
+            pair32<ENERGY>(dx, dy, dz, r2, in, sig2, eps24, eps24p, eps4, vsh, a);
+        }
+    }
+    if (nband) {
+        // pairs within rounding of r_cut: membership decided in FP64 from the
+        // master positions, as in the FP64 reference
+        for (int k = 0; k < n; ++k) {
+            const int h = nb[(long long)k * Pt];
+            float dx, dy, dz, r2;
+            sep_u<CUBIC>(pi, hpos[h], ry, rz, dx, dy, dz, r2);
+            if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, halo_slot(pc, np, h), R.L) < R.rc2)
+                pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, eps24p, eps4, vsh, a);
+        }
+    }
+    if (tooclose) err |= kErrFixed;
+}
+
+// a4 + a5: forces on every particle of a tile from its Verlet list, with
+// the neighbour positions read from the tile's halo in shared memory, then
+// the velocity-Verlet update of that particle.  Persistent blocks take tiles
+// from a work counter.
 template <int PREC, int MODE, bool ENERGY>
 __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) k_force(Bufs b)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Piece pc[kMaxPieces + 1];
+    __shared__ Tile tl;
+    __shared__ int s_tile, s_np;
     __shared__ double sm3[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
     if (b.ctl->err) return;
     const int cur = b.ctl->cur, nxt = cur ^ 1;
     const long long step = b.ctl->step;
-    const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
-    const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
     const double *X = b.x[cur];
-    // Fd * fscale is the force; FP32 mode keeps the exact fixed-point integer
-    // in Fd so that the 2^-22 scale folds into the kick constant
-    double Fd[3] = {0.0, 0.0, 0.0};
-    double fscale = 1.0;
-    double ui = 0.0, wi = 0.0, ki = 0.0;
+    const uint4 *P = b.pos[cur];
+    uint4 *hpos = reinterpret_cast<uint4 *>(smem_raw);
+    double *hx = reinterpret_cast<double *>(smem_raw);
+    double *hy = hx + b.hcap, *hz = hy + b.hcap;
+    unsigned short *lst = reinterpret_cast<unsigned short *>(smem_raw + (size_t)b.hcap * (PREC == 1 ? sizeof(uint4) : 3 * sizeof(double)));
     float ratio = 0.0f;
-    uint4 pi = make_uint4(0u, 0u, 0u, 0xffffffffu);
-    bool real = false;
     int err = 0;
-    if (i < b.S) {
-        pi = b.pos[cur][i];
-        real = (int)pi.w >= 0;
-    }
-    if (real) {
-        const int n = min(b.nn[i], b.K);
-        const int *nb = b.nbr + nbr_index(i, 0, b.K);   // entry k at nb[32 k]
-        if (PREC == 1) {
-            const uint4 *P = b.pos[cur];
-            const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
-            const float rc2_lo = R.rc2_lo, rc2_hi = R.rc2_hi, fmax2 = R.fmax2;
-            const float sig2 = R.sig2_f, eps24 = R.eps24_f, eps4 = R.eps4_f, vsh = R.vshift_f;
-            // a point half a box away on every axis: never within the cutoff
-            const uint4 far = make_uint4(pi.x ^ 0x80000000u, pi.y ^ 0x80000000u, pi.z ^ 0x80000000u, 0u);
-            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-            int nband = 0;
-            bool tooclose = false;
-            // neighbours in batches of kU: all index loads, then all position
-            // gathers, then branch-free arithmetic
-            for (int k0 = 0; k0 < n; k0 += kU) {
-                int jj[kU];
-                uint4 pj[kU];
-#pragma unroll
-                for (int u = 0; u < kU; ++u) jj[u] = (k0 + u < n) ? __ldg(nb + 32 * (k0 + u)) : 0;
-#pragma unroll
-                for (int u = 0; u < kU; ++u) pj[u] = (k0 + u < n) ? __ldg(P + jj[u]) : far;
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const float dx = (float)(int)(pi.x - pj[u].x) * qs0;
-                    const float dy = (float)(int)(pi.y - pj[u].y) * qs1;
-                    const float dz = (float)(int)(pi.z - pj[u].z) * qs2;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const bool in = r2 < rc2_lo;
-                    nband += (r2 < rc2_hi) & !in;
-                    tooclose |= r2 < fmax2;
-                    pair32<ENERGY>(dx, dy, dz, r2, in, sig2, eps24, eps4, vsh, a);
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+    __syncthreads();
+    for (;;) {
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= b.ctl->ntiles) break;
+        // the next tile is claimed now and published at the end of this one
+        int t_next = 0;
+        if (threadIdx.x == 0) t_next = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        load_tile(b, t, tl, pc, s_np);
+        __syncthreads();
+        const Replica &R = b.rep[tl.rep];
+        const int np = s_np;
+        const int Pt = tl.s1 - tl.s0;
+        if (pc[np].hoff > b.hcap) {          // the list build rejects such tiles first
+            err |= kErrList;
+            if (threadIdx.x == 0) s_tile = t_next;
+            __syncthreads();
+            continue;
+        }
+        if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
+        else stage_halo<double>(pc, np, [&](int h, int j) {
+            cp_async8(&hx[h], &X[j]);
+            cp_async8(&hy[h], &X[b.S + j]);
+            cp_async8(&hz[h], &X[2 * b.S + j]);
+        });
+        // the tile's lists: kmax rows of Pt entries, one contiguous block
+        const bool lstaged = tl.kmax <= kListStage && Pt <= kTileMax;
+        if (lstaged) {
+            const unsigned short *src = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
+            const int total = tl.kmax * Pt;            // entries; the block starts 64-byte aligned
+            const int nvec = total >> 3;
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(lst);
+            for (int m = threadIdx.x; m < nvec; m += blockDim.x) cp_async16(d4 + m, s4 + m);
+            for (int m = (nvec << 3) + threadIdx.x; m < total; m += blockDim.x) lst[m] = src[m];
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        double ui = 0.0, wi = 0.0, ki = 0.0;
+        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+            const uint4 pi = P[i];
+            const int n = min(b.nn[i], b.K);
+            const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
+            const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));   // entry k at nb[k Pt]
+            double Fd[3] = {0.0, 0.0, 0.0};
+            double fscale = 1.0;
+            if (PREC == 1) {
+                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                if (lstaged) {
+                    const unsigned short *nbs = lst + (i - tl.s0);
+                    if (R.cubic) neighbours32<ENERGY, true, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
+                    else neighbours32<ENERGY, false, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
+                } else {
+                    if (R.cubic) neighbours32<ENERGY, true, false>(R, hpos, nb, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
+                    else neighbours32<ENERGY, false, false>(R, hpos, nb, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
                 }
-            }
-            if (nband) {
-                // pairs within rounding of r_cut: membership decided in FP64
-                // from the master positions, as in the FP64 reference
+                const unsigned hs[3] = {a.hx, a.hy, a.hz}, ls[3] = {a.lx, a.ly, a.lz};
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    Fd[k] = (double)((long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k]);
+                fscale = kFixInv;
+                if (ENERGY) { ui += 0.5 * fx_value(a.hu, a.lu); wi += 0.5 * fx_value(a.hw, a.lw); }
+            } else {
+                const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
+                const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
+                const double h0 = 0.5 * L0, h1 = 0.5 * L1, h2 = 0.5 * L2;
+                const double eps24 = 24.0 * R.eps, eps4 = 4.0 * R.eps, sig2 = R.sigma * R.sigma;
+                const double rc2 = R.rc2, vsh = R.vshift;
+                const double band = 1e-12 * rc2;
+                const unsigned short *nbs = lst + (i - tl.s0);
                 for (int k = 0; k < n; ++k) {
-                    const int j = __ldg(nb + 32 * k);
-                    const uint4 q = __ldg(P + j);
-                    const float dx = (float)(int)(pi.x - q.x) * qs0;
-                    const float dy = (float)(int)(pi.y - q.y) * qs1;
-                    const float dz = (float)(int)(pi.z - q.z) * qs2;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 >= rc2_lo && r2 < rc2_hi && r2_exact(X, b.S, i, j, R.L) < R.rc2)
-                        pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, eps4, vsh, a);
-                }
-            }
-            if (tooclose) err |= kErrFixed;
-            const unsigned hh[3] = {a.hx, a.hy, a.hz}, ll[3] = {a.lx, a.ly, a.lz};
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                Fd[k] = (double)((long long)(int)hh[k] * 4194304LL + (long long)(int)ll[k]);
-            fscale = kFixInv;
-            if (ENERGY) { ui = 0.5 * fx_value(a.hu, a.lu); wi = 0.5 * fx_value(a.hw, a.lw); }
-        } else {
-            const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
-            const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
-            const double h0 = 0.5 * L0, h1 = 0.5 * L1, h2 = 0.5 * L2;
-            const double eps24 = 24.0 * R.eps, eps4 = 4.0 * R.eps, sig2 = R.sigma * R.sigma;
-            const double rc2 = R.rc2, vsh = R.vshift;
-            const double band = 1e-12 * rc2;
-            for (int k0 = 0; k0 < n; k0 += kU) {
-                int jj[kU];
-                double xj[kU][3];
-#pragma unroll
-                for (int u = 0; u < kU; ++u) jj[u] = (k0 + u < n) ? __ldg(nb + 32 * (k0 + u)) : -1;
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const long long j = jj[u] >= 0 ? jj[u] : i;
-                    xj[u][0] = __ldg(X + j);
-                    xj[u][1] = __ldg(X + b.S + j);
-                    xj[u][2] = __ldg(X + 2 * b.S + j);
-                }
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    double dx = xi0 - xj[u][0], dy = xi1 - xj[u][1], dz = xi2 - xj[u][2];
+                    const int h = lstaged ? nbs[k * Pt] : __ldg(nb + (long long)k * Pt);
+                    double dx = xi0 - hx[h], dy = xi1 - hy[h], dz = xi2 - hz[h];
                     dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
                     dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
                     dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
                     const double r2 = dx * dx + dy * dy + dz * dz;
-                    if (jj[u] >= 0 && r2 < rc2 + band) {
+                    if (r2 < rc2 + band) {
                         bool in = r2 < rc2 - band;
-                        if (!in) in = r2_exact(X, b.S, i, jj[u], R.L) < rc2;
+                        if (!in) in = r2_exact(X, b.S, i, halo_slot(pc, np, h), R.L) < rc2;
                         if (in) {
                             const double ir2 = 1.0 / r2;
                             const double s2 = sig2 * ir2;
@@ -386,113 +453,104 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                         }
                     }
                 }
+                if (!isfinite(Fd[0]) || !isfinite(Fd[1]) || !isfinite(Fd[2])) err |= kErrNonfinite;
             }
-            if (!isfinite(Fd[0]) || !isfinite(Fd[1]) || !isfinite(Fd[2])) err |= kErrNonfinite;
-        }
-        // FENE bonds of this particle (Sec. 4), both ends of every bond visited;
-        // in FP32 mode the bond force joins the same fixed-point sum
-        if (b.has_bonds) {
-            const int id = (int)pi.w;
-            for (int q = b.bond_off[id]; q < b.bond_off[id + 1]; ++q) {
-                const int sj = b.slot_of_id[b.bond_partner[q]];
-                if (PREC == 1) {
-                    const uint4 pj = b.pos[cur][sj];
-                    const float dx = (float)(int)(pi.x - pj.x) * R.qs[0];
-                    const float dy = (float)(int)(pi.y - pj.y) * R.qs[1];
-                    const float dz = (float)(int)(pi.z - pj.z) * R.qs[2];
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float qf = 1.0f - r2 / b.fene_R02_f;
-                    if (!(qf > 0.0f)) { err |= kErrBond; continue; }
-                    const float c = -b.fene_K_f / qf;
-                    unsigned h = 0, l = 0;
-                    fx_acc2(c, dx, h, l); Fd[0] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
-                    fx_acc2(c, dy, h, l); Fd[1] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
-                    fx_acc2(c, dz, h, l); Fd[2] += (double)((long long)(int)h * 4194304LL + (long long)(int)l);
-                    if (ENERGY) {
-                        ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log((double)qf));
-                        wi += 0.5 * (double)(c * r2);
-                    }
-                } else {
-                    double d[3];
-                    for (int k = 0; k < 3; ++k) {
-                        double t = X[k * b.S + i] - X[k * b.S + sj];
-                        d[k] = t - R.L[k] * rint(t / R.L[k]);
-                    }
-                    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    const double qd = 1.0 - r2 / b.fene_R02;
-                    if (!(qd > 0.0)) { err |= kErrBond; continue; }
-                    const double c = -b.fene_K / qd;
-                    for (int k = 0; k < 3; ++k) Fd[k] += c * d[k];
-                    if (ENERGY) {
-                        ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log(qd));
-                        wi += 0.5 * c * r2;
+            // FENE bonds of this particle (Sec. 4), both ends of every bond
+            // visited; in FP32 mode the bond force joins the fixed-point sum
+            if (b.has_bonds) {
+                const int id = (int)pi.w;
+                for (int q = b.bond_off[id]; q < b.bond_off[id + 1]; ++q) {
+                    const int sj = b.slot_of_id[b.bond_partner[q]];
+                    if (PREC == 1) {
+                        const uint4 pj = P[sj];
+                        const float dx = (float)(int)(pi.x - pj.x) * R.qs[0];
+                        const float dy = (float)(int)(pi.y - pj.y) * R.qs[1];
+                        const float dz = (float)(int)(pi.z - pj.z) * R.qs[2];
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float qf = 1.0f - r2 / b.fene_R02_f;
+                        if (!(qf > 0.0f)) { err |= kErrBond; continue; }
+                        const float c = -b.fene_K_f / qf;
+                        unsigned h = 0, l = 0;
+                        fx_acc2(c, dx, h, l); Fd[0] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
+                        fx_acc2(c, dy, h, l); Fd[1] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
+                        fx_acc2(c, dz, h, l); Fd[2] += (double)((long long)(int)h * 4194304LL + (long long)(int)l);
+                        if (ENERGY) {
+                            ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log((double)qf));
+                            wi += 0.5 * (double)(c * r2);
+                        }
+                    } else {
+                        double d[3];
+                        for (int k = 0; k < 3; ++k) {
+                            double tt = X[k * b.S + i] - X[k * b.S + sj];
+                            d[k] = tt - R.L[k] * rint(tt / R.L[k]);
+                        }
+                        const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        const double qd = 1.0 - r2 / b.fene_R02;
+                        if (!(qd > 0.0)) { err |= kErrBond; continue; }
+                        const double c = -b.fene_K / qd;
+                        for (int k = 0; k < 3; ++k) Fd[k] += c * d[k];
+                        if (ENERGY) {
+                            ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log(qd));
+                            wi += 0.5 * c * r2;
+                        }
                     }
                 }
             }
-        }
-
-        double v[3];
-        if (MODE != kModeOut) {
+            double v[3];
+            if (MODE != kModeOut) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) v[k] = b.v[cur][k * b.S + i];
-            if (b.langevin) {
-                for (int k = 0; k < 3; ++k) Fd[k] *= fscale;
-                fscale = 1.0;
-                langevin(b, (int)pi.w, step, v, Fd);
+                for (int k = 0; k < 3; ++k) v[k] = b.v[cur][k * b.S + i];
+                if (b.langevin) {
+                    for (int k = 0; k < 3; ++k) Fd[k] *= fscale;
+                    fscale = 1.0;
+                    langevin(b, (int)pi.w, step, v, Fd);
+                }
+            }
+            if (MODE == kModeOut) {
+                const int id = (int)pi.w;
+                if (b.fout)
+                    for (int k = 0; k < 3; ++k) b.fout[k * b.N + id] = Fd[k] * fscale;
+                if (ENERGY)
+                    for (int k = 0; k < 3; ++k) { double w = b.v[cur][k * b.S + i]; ki += 0.5 * b.mass * w * w; }
+            } else if (MODE == kModeStore) {
+                for (int k = 0; k < 3; ++k) b.F[k * b.S + i] = Fd[k] * fscale;
+                if (ENERGY) for (int k = 0; k < 3; ++k) ki += 0.5 * b.mass * v[k] * v[k];
+            } else if (MODE == kModeFinal) {
+                const double c = b.half_dt_over_m * fscale;
+                for (int k = 0; k < 3; ++k) {
+                    v[k] += c * Fd[k];
+                    b.v[cur][k * b.S + i] = v[k];
+                    b.F[k * b.S + i] = Fd[k] * fscale;
+                    if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
+                }
+            } else {  // kModeFused: end of step n, then the first half kick and drift of step n + 1
+                const double c = b.half_dt_over_m * fscale;
+                double xi[3];
+                for (int k = 0; k < 3; ++k) {
+                    v[k] += c * Fd[k];
+                    if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
+                    v[k] += c * Fd[k];
+                    xi[k] = X[k * b.S + i];
+                }
+                ratio = fmaxf(ratio, drift(b, R, i, nxt, pi.w, xi, v));
             }
         }
-        if (MODE == kModeOut) {
-            const int id = (int)pi.w;
-            if (b.fout)
-                for (int k = 0; k < 3; ++k) b.fout[k * b.N + id] = Fd[k] * fscale;
-            if (ENERGY)
-                for (int k = 0; k < 3; ++k) { double w = b.v[cur][k * b.S + i]; ki += 0.5 * b.mass * w * w; }
-        } else if (MODE == kModeStore) {
-            for (int k = 0; k < 3; ++k) b.F[k * b.S + i] = Fd[k] * fscale;
-            if (ENERGY) for (int k = 0; k < 3; ++k) ki += 0.5 * b.mass * v[k] * v[k];
-        } else if (MODE == kModeFinal) {
-            const double c = b.half_dt_over_m * fscale;
-            for (int k = 0; k < 3; ++k) {
-                v[k] += c * Fd[k];
-                b.v[cur][k * b.S + i] = v[k];
-                b.F[k * b.S + i] = Fd[k] * fscale;
-                if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
+        if (ENERGY) {
+            double a = ui, c = ki, d = wi;
+            block_sum3(a, c, d, sm3);
+            if (threadIdx.x == 0) {
+                b.partial[4 * t + 0] = a;
+                b.partial[4 * t + 1] = c;
+                b.partial[4 * t + 2] = d;
             }
-        } else {  // kModeFused: end of step n and first half kick of step n + 1
-            const double c = b.half_dt_over_m * fscale;
-            double xi[3];
-            for (int k = 0; k < 3; ++k) {
-                v[k] += c * Fd[k];                        // synchronised v_n
-                if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
-                v[k] += c * Fd[k];
-                xi[k] = X[k * b.S + i];
-            }
-            ratio = drift(b, R, i, nxt, pi.w, xi, v);
         }
-    } else if (MODE == kModeFused && i < b.S) {
-        b.pos[nxt][i] = pi;   // padding slot: keep the id marker in the other buffer
+        if (threadIdx.x == 0) s_tile = t_next;
+        __syncthreads();   // the halo and the tile record are reused by the next tile
     }
     if (err) atomicOr(&b.ctl->err, err);
-
-    if (ENERGY) {
-        double a = ui, c = ki, d = wi;
-        block_sum3(a, c, d, sm3);
-        if (threadIdx.x == 0) {
-            b.partial[4 * blockIdx.x + 0] = a;
-            b.partial[4 * blockIdx.x + 1] = c;
-            b.partial[4 * blockIdx.x + 2] = d;
-        }
-    }
     constexpr bool kDrift = (MODE == kModeFused);
-    if (kDrift) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ratio = fmaxf(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
-        if ((threadIdx.x & 31) == 0) smr[threadIdx.x >> 5] = ratio;
-        __syncthreads();
-        if (threadIdx.x == 0)
-            for (int q = 1; q < kBlock / 32; ++q) ratio = fmaxf(ratio, smr[q]);
-    }
-    finish(b, kDrift, ENERGY, ratio);
+    if (kDrift) ratio = block_max(ratio, smr);
+    finish(b, kDrift, ENERGY, true, ratio);
 }
 
 // Integrate1 of the first step of an md_step call: v += dt/2m F; x += dt v.
@@ -513,26 +571,45 @@ __global__ void __launch_bounds__(kBlock) k_kick_drift(Bufs b)
                 xi[k] = b.x[cur][k * b.S + i];
             }
             ratio = drift(b, R, i, nxt, pi.w, xi, v);
-        } else {
-            b.pos[nxt][i] = pi;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ratio = fmaxf(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
-    if ((threadIdx.x & 31) == 0) smr[threadIdx.x >> 5] = ratio;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int q = 1; q < kBlock / 32; ++q) ratio = fmaxf(ratio, smr[q]);
-    finish(b, true, false, ratio);
+    ratio = block_max(ratio, smr);
+    finish(b, true, false, false, ratio);
+}
+
+// grid of a persistent kernel: resident blocks per SM x SMs
+static int persistent_grid(const void *fn, int block, size_t smem)
+{
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // the default 48 KB limit covers static plus dynamic shared memory: always opt in
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem);
+    return (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
+}
+
+template <int PREC, int MODE, bool ENERGY>
+static void launch_one(const Bufs &b, cudaStream_t st)
+{
+    const size_t smem = (size_t)b.hcap * (PREC == 1 ? sizeof(uint4) : 3 * sizeof(double)) +
+                        (size_t)kListStage * kTileMax * sizeof(unsigned short);
+    static int grid = 0;
+    static size_t grid_smem = 0;
+    if (grid == 0 || grid_smem != smem) {
+        grid = persistent_grid((const void *)k_force<PREC, MODE, ENERGY>, kBlock, smem);
+        grid_smem = smem;
+    }
+    k_force<PREC, MODE, ENERGY><<<grid, kBlock, smem, st>>>(b);
 }
 
 template <int PREC>
 static void launch_force_p(const Bufs &b, int mode, bool energy, cudaStream_t st)
 {
-#define MDK_CASE(M)                                                                         \
-    case M:                                                                                 \
-        if (energy) k_force<PREC, M, true><<<b.nblk, kBlock, 0, st>>>(b);                   \
-        else k_force<PREC, M, false><<<b.nblk, kBlock, 0, st>>>(b);                         \
+#define MDK_CASE(M)                                        \
+    case M:                                                \
+        if (energy) launch_one<PREC, M, true>(b, st);      \
+        else launch_one<PREC, M, false>(b, st);            \
         break;
     switch (mode) {
         MDK_CASE(kModeOut)

@@ -4,6 +4,7 @@
 // sequence of one velocity-Verlet step (Fig. 1).
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -26,7 +27,7 @@ struct md_handle {
     bool state_set = false;
     bool F_valid = false;
     long long N = 0, S = 0;
-    int C = 0, nblk = 0, K = 0;
+    int C = 0, nblk = 0, K = 0, nrows = 0;
     double *stage = nullptr;        // 6 * N doubles: in/out staging
     double *thermo_stage = nullptr; // grows on demand
     long long thermo_cap = 0;
@@ -101,7 +102,7 @@ md_status alloc_list(md_handle *h, int K)
     }
     h->K = K;
     h->b.K = K;
-    h->b.nbr = dalloc<int>(h, (size_t)K * (size_t)h->S);
+    h->b.nbr = dalloc<unsigned short>(h, (size_t)K * (size_t)h->S);
     if (!h->b.nbr) return fail(h, MD_ERR_CUDA, "cannot allocate the neighbour list");
     return MD_OK;
 }
@@ -155,7 +156,7 @@ md_status md_create(const md_params *p, md_handle **out)
     const int nrep = p->n_replicas;
     h->offsets.assign(p->replica_offsets, p->replica_offsets + nrep + 1);
     long long slot = 0;
-    int cell = 0;
+    int cell = 0, rows = 0;
     for (int r = 0; r < nrep; ++r) {
         long long n = h->offsets[r + 1] - h->offsets[r];
         if (n < 0 || n > (1LL << 30)) { delete h; return MD_ERR_ARG; }
@@ -186,6 +187,8 @@ md_status md_create(const md_params *p, md_handle **out)
         R.cell_off = cell;
         R.ncells = R.ncell[0] * R.ncell[1] * R.ncell[2];
         cell += R.ncells;
+        R.row_off = rows;
+        rows += R.ncell[1] * R.ncell[2];
         R.slot_begin = slot;
         R.n = n;
         R.id_begin = h->offsets[r];
@@ -221,11 +224,23 @@ md_status md_create(const md_params *p, md_handle **out)
             if (lj_fmag(mid, eps, sig) > std::ldexp(1.0, 21) * 0.9) lo = mid; else hi = mid;
         }
         R.fmax2 = (float)(hi * hi);
+        const double u = R.L[0] / 4294967296.0;   // fixed-point unit of the x axis
+        R.cubic = (R.L[0] == R.L[1] && R.L[0] == R.L[2]) ? 1 : 0;
+        R.ry = (float)(R.L[1] / R.L[0]);
+        R.rz = (float)(R.L[2] / R.L[0]);
+        R.rc2_lo_u = (float)((rc * rc - brc) / (u * u));
+        R.rc2_hi_u = (float)((rc * rc + brc) / (u * u));
+        R.fmax2_u = (float)(hi * hi / (u * u));
+        R.sig2_u = (float)(sig * sig / (u * u));
+        R.eps24_u = (float)(24.0 * eps / u);
+        R.rl2_lo_u = (float)((rl * rl - brl) / (u * u));
+        R.rl2_hi_u = (float)((rl * rl + brl) / (u * u));
         h->reps.push_back(R);
     }
     h->N = h->offsets[nrep];
     h->S = slot;
     h->C = cell;
+    h->nrows = rows;
     h->nblk = (int)(slot / mdk::kBlock);
     if (h->N < 1) { delete h; return MD_ERR_ARG; }
 
@@ -252,11 +267,23 @@ md_status md_create(const md_params *p, md_handle **out)
         }
         K = (int)round_up((long long)std::ceil(kmax) + 32, 32);
     }
+    if (K > 65535) { delete h; return MD_ERR_ARG; }
+
+    // halo capacity of the tile kernels: 3 x 3 rows of a full tile of
+    // kTileMax particles plus two cells' worth at the mean occupancy (the
+    // tiler keeps every halo within it; md_build_neighbors grows it when one
+    // cell's halo alone does not fit)
+    double occ = 0;
+    for (auto &R : h->reps) occ = std::fmax(occ, R.ncells ? (double)R.n / R.ncells : 0.0);
+    int hcap = (int)round_up((long long)(9.0 * (mdk::kTileMax + 2.0 * occ + 16.0)), 128);
+    hcap = std::min(std::max(hcap, 1024), 8192);
 
     Bufs &b = h->b;
     b.S = h->S;
     b.N = h->N;
     b.C = h->C;
+    b.nrows = h->nrows;
+    b.hcap = hcap;
     b.nrep = nrep;
     b.nblk = h->nblk;
     b.dt = p->dt;
@@ -287,7 +314,13 @@ md_status md_create(const md_params *p, md_handle **out)
     ok &= (b.cell_end = dalloc<int>(h, h->C)) != nullptr;
     ok &= (b.bucket = dalloc<int>(h, h->S)) != nullptr;
     ok &= (b.nn = dalloc<int>(h, h->S)) != nullptr;
-    ok &= (b.partial = dalloc<double>(h, 4 * (size_t)h->nblk)) != nullptr;
+    ok &= (b.partial = dalloc<double>(h, 4 * (size_t)h->C)) != nullptr;
+    ok &= (b.tiles = dalloc<mdk::Tile>(h, h->C)) != nullptr;
+    ok &= (b.pieces = dalloc<mdk::Piece>(h, (size_t)h->C * (mdk::kMaxPieces + 1))) != nullptr;
+    ok &= (b.tile_np = dalloc<int>(h, h->C)) != nullptr;
+    ok &= (b.row_tiles = dalloc<int>(h, h->nrows + 1)) != nullptr;
+    ok &= (b.rep_tile = dalloc<int>(h, nrep + 1)) != nullptr;
+    ok &= (b.row_rep = dalloc<int>(h, h->nrows)) != nullptr;
     ok &= (b.ctl = dalloc<Ctl>(h, 1)) != nullptr;
     ok &= (h->stage = dalloc<double>(h, 6 * h->N)) != nullptr;
     ok &= (h->d_count = dalloc<unsigned long long>(h, 1)) != nullptr;
@@ -298,6 +331,10 @@ md_status md_create(const md_params *p, md_handle **out)
     std::vector<int> blk(h->nblk, 0);
     for (int r = 0; r < nrep; ++r)
         for (int q = h->reps[r].blk_begin; q < h->reps[r].blk_end; ++q) blk[q] = r;
+    std::vector<int> rowrep(h->nrows, 0);
+    for (int r = 0; r < nrep; ++r)
+        for (int q = 0; q < h->reps[r].ncell[1] * h->reps[r].ncell[2]; ++q) rowrep[h->reps[r].row_off + q] = r;
+    ok &= cudaMemcpy(b.row_rep, rowrep.data(), sizeof(int) * h->nrows, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(drep, h->reps.data(), sizeof(Replica) * nrep, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(dblk, blk.data(), sizeof(int) * h->nblk, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemset(b.cell_count, 0, sizeof(int) * h->C) == cudaSuccess;
@@ -391,13 +428,20 @@ md_status md_build_neighbors(md_handle *h, void *stream)
     if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
     if (read_ctl(h, &c) != MD_OK) return MD_ERR_CUDA;
     if ((c.err & mdk::kErrList) && c.err == mdk::kErrList) {
-        int K = (int)round_up((long long)(c.max_nn * 1.25) + 32, 32);
-        if (alloc_list(h, K) != MD_OK) return MD_ERR_CUDA;
+        if (c.max_nn > h->K) {
+            int K = (int)round_up((long long)(c.max_nn * 1.25) + 32, 32);
+            if (K > 65535 || alloc_list(h, K) != MD_OK) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list too long");
+        }
+        if (c.max_halo > h->b.hcap) {
+            const int lim = (h->precision == MD_FP32_FIXED) ? 12288 : 8192;   // shared memory per block
+            int hc = (int)round_up((long long)(c.max_halo * 1.25), 128);
+            if (c.max_halo > lim) return fail(h, MD_ERR_LIST_OVERFLOW, "a cell neighbourhood exceeds the halo capacity");
+            h->b.hcap = std::min(hc, lim);
+        }
         int zero = 0;
         if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
             return MD_ERR_CUDA;
-        // the overflowing build still sorted the state and counted every list;
-        // only the entries beyond the old capacity were dropped: build again
+        // the overflowing build still sorted the state; build again with the larger capacities
         mdk::launch_set_rebuild(h->b, st);
         mdk::launch_rebuild_chain(h->b, st);
         return sync_and_check(h, st);

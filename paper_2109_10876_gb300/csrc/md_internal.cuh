@@ -11,10 +11,18 @@
 //                  int32 is the minimum-image separation in units of L_k / 2^32,
 //                  exact, with the periodic wrap done by integer overflow.
 //   xref           uint4 per slot: pos at the last list build (displacement check).
-//   nbr, nn        Verlet list in warp slices: the lists of slots 32w .. 32w+31
-//                  form one contiguous block of K rows of 32 entries, entry k of
-//                  slot s at nbr[(s / 32) * 32 K + 32 k + s % 32]; nn[s] entries.
-//                  A warp reads its 32 lists as one contiguous stream.
+//   tiles          runs of consecutive cells along an x-row of a replica grid,
+//                  cut at every rebuild so that a tile holds at most kTileMax
+//                  particles and its halo (the tile's cells widened by one cell
+//                  in x, on the 3 x 3 neighbouring rows) at most Hcap particles.
+//                  A tile's particles are one contiguous slot range; its halo
+//                  is a fixed sequence of contiguous slot ranges ("pieces").
+//   nbr, nn        Verlet list of 16-bit halo indices, by tile: the lists of a
+//                  tile's P = s1 - s0 particles occupy nbr[s0 K, s1 K) as K rows
+//                  of P entries, entry k of particle p = s - s0 at
+//                  nbr[s0 K + k P + p]; the threads of a tile read a row as one
+//                  contiguous run.  nn[s] entries, padded with the particle's
+//                  own halo index up to a multiple of kPad.
 //   cells          count / start / end per cell of every replica grid.
 #pragma once
 #include <cstdint>
@@ -24,6 +32,8 @@ namespace mdk {
 
 constexpr int kBlock = 128;          // threads per block of the per-slot kernels
 constexpr int kMaxReplicas = 4096;
+constexpr int kTileMax = 128;        // particles per tile (one per thread)
+constexpr int kMaxPieces = 18;       // 3 x 3 rows, at most 2 x-pieces each
 
 // error bits latched in Ctl::err
 enum : int {
@@ -43,6 +53,7 @@ struct Replica {
     int ncell[3];         // cell grid, edge L / ncell >= r_cut + r_skin
     int cell_off;         // first global cell index of this replica
     int ncells;
+    int row_off;          // first global row (rows = (cy, cz) pairs, cz-major)
     long long slot_begin; // first slot
     long long n;          // real particles
     long long id_begin;   // first particle id (caller numbering)
@@ -54,7 +65,12 @@ struct Replica {
     float rc2_lo, rc2_hi;                 // FP32 band around rc^2 resolved in FP64
     float rl2_lo, rl2_hi;                 // FP32 band around (r_cut + r_skin)^2
     float disp2_thr;                      // (r_skin / 2)^2, minus a margin
-    float fmax2;                          // largest r^-2 (smallest r) the fixed-point range covers
+    float fmax2;                          // smallest r^2 the fixed-point range covers
+    // the same constants with lengths in fixed-point units of the x axis
+    // (u = L_x / 2^32), used by the FP32 pair loop: r2 and d stay in u
+    int cubic;                            // all box edges equal: no per-axis scaling
+    float ry, rz;                         // L_y / L_x, L_z / L_x
+    float rc2_lo_u, rc2_hi_u, fmax2_u, sig2_u, eps24_u, rl2_lo_u, rl2_hi_u;
 };
 
 // Device control block: every per-step decision lives here, so a step needs
@@ -69,16 +85,82 @@ struct Ctl {
     unsigned done_kick;
     int max_occ;             // largest cell occupancy at the last build
     int max_nn;              // longest list at the last build
-    int pad0;
+    int ntiles;              // tiles of the current build
+    unsigned tile_next;      // work counter of the persistent tile kernels
+    int max_halo;            // largest halo of the current build
     long long step;          // index of the current positions x_step
     long long rebuilds;
     long long list_entries;
 };
 
-// index of entry k of slot s in the sliced list
-__host__ __device__ __forceinline__ long long nbr_index(long long s, int k, int K)
+// A tile: row (cy, cz) of replica rep, cells [x0, x1) along x, particles in
+// slots [s0, s1), halo of hsize particles.
+struct Tile {
+    int rep, cy, cz, x0, x1, s0, s1, hsize;
+    int kmax;   // longest padded list of the tile (written by the list build)
+};
+
+constexpr int kListStage = 88;       // list rows of a tile staged in shared memory
+
+// One contiguous slot range of a halo: cells [xa, xb) of halo row `row`,
+// placed at halo offset hoff.
+struct Piece {
+    int row, xa, xb, slot0, hoff, n;
+};
+
+// Unique neighbour offsets along an axis with n cells: {-1, 0, 1}, {0, 1} or {0}.
+__host__ __device__ __forceinline__ void axis_offsets(int n, int &lo, int &cnt)
 {
-    return (s >> 5) * (32LL * K) + 32LL * k + (s & 31);
+    if (n >= 3) { lo = -1; cnt = 3; }
+    else if (n == 2) { lo = 0; cnt = 2; }
+    else { lo = 0; cnt = 1; }
+}
+
+__host__ __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Pieces of the halo of cells [x0, x1) on row (cy, cz): for each of the (up
+// to) 3 x 3 rows in (dz, dy) order, the cells [x0 - 1, x1] along x (the whole
+// row when that covers it), split at the periodic boundary.  Returns the
+// number of pieces; fills p[] with their slot ranges and halo offsets.
+__device__ __forceinline__ int halo_pieces(const int *cell_start, const int *cell_end, int cell_off,
+                                           const int ncell[3], int cy, int cz, int x0, int x1, Piece *p,
+                                           int *hsize = nullptr)
+{
+    const int nx = ncell[0], ny = ncell[1], nz = ncell[2];
+    int ly, cntY, lz, cntZ;
+    axis_offsets(ny, ly, cntY);
+    axis_offsets(nz, lz, cntZ);
+    int np = 0, h = 0, row = 0;
+    for (int oz = 0; oz < cntZ; ++oz) {
+        const int zz = wrapi(cz + lz + oz, nz);
+        for (int oy = 0; oy < cntY; ++oy, ++row) {
+            const int yy = wrapi(cy + ly + oy, ny);
+            const int base = cell_off + (zz * ny + yy) * nx;
+            int ra[2], rb[2], nr = 0;
+            if (x1 - x0 + 2 >= nx) { ra[0] = 0; rb[0] = nx; nr = 1; }
+            else if (x0 == 0) { ra[0] = nx - 1; rb[0] = nx; ra[1] = 0; rb[1] = x1 + 1; nr = 2; }
+            else if (x1 == nx) { ra[0] = x0 - 1; rb[0] = nx; ra[1] = 0; rb[1] = 1; nr = 2; }
+            else { ra[0] = x0 - 1; rb[0] = x1 + 1; nr = 1; }
+            for (int q = 0; q < nr; ++q) {
+                const int s0 = cell_start[base + ra[q]];
+                const int n = cell_end[base + rb[q] - 1] - s0;
+                if (p) { p[np].row = row; p[np].xa = ra[q]; p[np].xb = rb[q]; p[np].slot0 = s0; p[np].hoff = h; p[np].n = n; }
+                ++np;
+                h += n;
+            }
+        }
+    }
+    if (p) p[np].hoff = h;   // total halo size after the last piece
+    if (hsize) *hsize = h;
+    return np;
+}
+
+constexpr int kPad = 4;              // lists are padded to a multiple of this
+
+// index of entry k of the particle p of a tile starting at slot s0 with P particles
+__host__ __device__ __forceinline__ long long nbr_index(long long s0, int P, int K, int k, int p)
+{
+    return s0 * K + (long long)k * P + p;
 }
 
 // Everything the kernels touch.  Plain pointers; sizes in slots S, cells C,
@@ -94,14 +176,22 @@ struct Bufs {
     int *cell_count;         // C
     int *cell_start;         // C
     int *cell_end;           // C (cursor during the scatter, then one past the last slot)
+    int *row_rep;            // nrows: replica of every row (rows ordered by replica)
     int *bucket;             // S
-    int *nbr;                // K * S
+    unsigned short *nbr;     // K * S halo indices
     int *nn;                 // S
+    Tile *tiles;             // C (a tile has at least one cell)
+    Piece *pieces;           // kMaxPieces + 1 per tile: the halo pieces, then the total in [np].hoff
+    int *tile_np;            // pieces per tile
+    int *row_tiles;          // rows: tiles per row, then their exclusive scan
+    int *rep_tile;           // nrep + 1: first tile of every replica
+    int nrows;               // rows over all replicas
+    int hcap;                // halo capacity (particles) of the tile kernels
     const Replica *rep;      // n_rep
     const int *blk_rep;      // replica of every block of kBlock slots
     const int *bond_off;     // N + 1, bonds of particle id (both directions)
     const int *bond_partner; // 2 * n_bonds particle ids
-    double *partial;         // 4 per block: U, K, W partial sums
+    double *partial;         // 4 per tile: U, K, W partial sums
     double *thermo;          // where the last block writes (U, K, W) per replica, or null
     double *fout;            // force output in caller order (3 * N) or null
     Ctl *ctl;
@@ -115,6 +205,48 @@ struct Bufs {
     float fene_K_f, fene_R02_f;
     unsigned long long seed;
 };
+
+// Asynchronous global -> shared copies (no register staging): every copy a
+// block issues is in flight at once; cp_async_wait_all waits for this
+// thread's copies (a hardware wait), to be followed by __syncthreads().
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Cooperative load of a tile record and its halo pieces into shared memory.
+__device__ __forceinline__ void load_tile(const Bufs &b, int t, Tile &tl, Piece *pc, int &np)
+{
+    if (threadIdx.x == 0) { tl = b.tiles[t]; np = b.tile_np[t]; }
+    const int *src = reinterpret_cast<const int *>(b.pieces + (size_t)t * (kMaxPieces + 1));
+    int *dst = reinterpret_cast<int *>(pc);
+    constexpr int words = (kMaxPieces + 1) * sizeof(Piece) / sizeof(int);
+    for (int m = threadIdx.x; m < words; m += blockDim.x) dst[m] = src[m];
+}
+
+// Flat copy of a tile's halo (all loads independent): element h of piece q.
+template <class T, class F>
+__device__ __forceinline__ void stage_halo(const Piece *pc, int np, F load)
+{
+    const int H = pc[np].hoff;
+    int q = 0;
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        while (h >= pc[q + 1].hoff) ++q;   // pieces in ascending halo order
+        load(h, pc[q].slot0 + (h - pc[q].hoff));
+    }
+}
 
 // kernel modes of the force kernel
 enum Mode : int {
