@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the short-range MD hot path on GB300.
+
+Workload (the LJ fluid at scale): N = 2,048,000 particles on an fcc lattice
+(80^3 cells x 4), reduced density 0.8442, Gaussian velocities at T* = 0.72
+with zero net momentum (seeded), Lennard-Jones with eps = sigma = 1 and
+r_cut = 2.5 sigma shifted to zero energy at r_cut, Verlet skin 0.3 sigma,
+velocity Verlet at dt = 0.005, NVE.  One bench step is one MD step: the
+device-side cell sort / Verlet-list rebuild when triggered, and the fused
+pair-force + velocity-Verlet kernel, FP32 pair arithmetic with 64-bit
+fixed-point force sums and FP64 positions / velocities.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs independent replicas (one 2.048M system per rank, seeds differ;
+no data-path collective) under torch.distributed.run; the value is the
+whole-job particle-steps/s over the slowest rank.  `--impl reference` times
+the FP64 CPU oracle on bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LJ force+integrate particle-steps/s at 2M atoms; % HBM roofline; FP32 vs FP64"
+UNIT = "particle-steps/s"
+NCELL = 80
+RHO, T0, RC, SKIN, DT = 0.8442, 0.72, 2.5, 0.3, 0.005
+# per particle and fused step, algorithmic HBM bytes of the force kernel
+# besides the list: own fixed-point position 16, list length 4, x read+write 48,
+# v read+write 48, new fixed-point position 16, build-time position 16
+FORCE_FIXED_BYTES = 16 + 4 + 48 + 48 + 16 + 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ncell", type=int, default=NCELL)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64, CPU baseline and force error")
+    return ap.parse_args()
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2109_10876_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        m = json.load(open(p))
+        return float(m["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(digest):
+    """DRAM bytes per particle of the fused force kernel from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "force_fp32_fused_lj_fluid.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    if vals.get("csrc_sha") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_particle"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[4 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(x, box, target_s=10.0):
+    """The FP64 oracle (as it stands) on a bounded sample of the workload: exact
+    forces on S particles, each summed over all N particles.  S particle-steps
+    of work; S is sized from a short calibration so the sample takes about
+    target_s seconds of the host's cores."""
+    import oracle
+    n = len(x)
+    s = oracle.System(n, box, rc=RC)
+    rng = np.random.default_rng(123)
+    t0 = time.perf_counter()
+    oracle.forces_sample(s, x, rng.choice(n, 16, replace=False))
+    per = max((time.perf_counter() - t0) / 16, 1e-6)
+    S = int(min(max(16, target_s / per), n))
+    idx = rng.choice(n, S, replace=False)
+    t0 = time.perf_counter()
+    oracle.forces_sample(s, x, idx)
+    t = time.perf_counter() - t0
+    return {"value": S / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"exact FP64 O(N^2) forces on {S} sampled particles of the N={n} system "
+                      f"(one particle-step each), {t:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2109_10876_gb300 import inputs
+    x, v, box = inputs.lj_fluid(args.ncell, rho=RHO, T=T0, seed=2)
+    n = len(x)
+    s = oracle.System(n, box, rc=RC)
+    rng = np.random.default_rng(7)
+    t0 = time.perf_counter()
+    oracle.forces_sample(s, x, rng.choice(n, 8, replace=False))
+    per = max((time.perf_counter() - t0) / 8, 1e-6)
+    budget = 120.0                                   # whole run, seconds
+    S = int(max(4, min(n, budget / per / max(args.steps + args.warmup, 1))))
+    for _ in range(args.warmup):
+        oracle.forces_sample(s, x, rng.choice(n, S, replace=False))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forces_sample(s, x, rng.choice(n, S, replace=False))
+    t = time.perf_counter() - t0
+    val = S * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"LJ fluid N={n} fcc, rho={RHO}, T*={T0}, rc={RC}, skin={SKIN}, dt={DT}, NVE",
+                       "sample_particles_per_step": S},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"per step: exact FP64 forces on {S} sampled particles, each over all N"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_2109_10876_gb300 import inputs
+    from paper_2109_10876_gb300 import md
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    x, v, box = inputs.lj_fluid(args.ncell, rho=RHO, T=T0, seed=2 + rank)
+    n = len(x)
+    xt = torch.tensor(x.T.copy(), device=dev)
+    vt = torch.tensor(v.T.copy(), device=dev)
+
+    # ---- device-resident timed run (FP32 pair math + fixed-point sums)
+    h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+    md.md_set_state(h, xt, vt)
+    md.md_build_neighbors(h)
+    md.md_step(h, max(args.warmup, 3))
+    md.md_sync(h)
+    st0 = md.md_get_stats(h)
+    md.md_set_timing(h, True)
+    clocks = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    md.md_step(h, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st1 = md.md_get_stats(h)
+    sect_ms, sect_n = md.md_get_timing(h)
+    ms_max = barrier_max(ms, world)
+    value = world * n * args.steps / (ms_max * 1e-3)
+
+    # ---- roofline of the dominant kernel (fused force + velocity Verlet)
+    mean_nn = st1["list_entries"] / n
+    pad = 4
+    list_bytes = 2.0 * (mean_nn + (pad - 1) / 2.0)
+    bytes_pp = FORCE_FIXED_BYTES + list_bytes
+    force_ms = sect_ms[md.MD_SECT_FORCE] / max(sect_n[md.MD_SECT_FORCE], 1)
+    achieved = n * bytes_pp / (force_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    digest = csrc_digest()
+    tpp = profiled_traffic(digest)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None if tpp is None else round(tpp * n),
+                "peak_source": peak_kind, "kernel": "k_force<FP32, fused>",
+                "algorithmic_bytes_per_particle": round(bytes_pp, 1),
+                "launch_ms": round(force_ms, 4)}
+
+    extras = {}
+    if not args.no_extras:
+        # ---- end to end through the C ABI with pinned host buffers: upload the
+        # state, build, K steps with (U, K, W) every step, download the state
+        xh = torch.tensor(x.T.copy()).pin_memory()
+        vh = torch.tensor(v.T.copy()).pin_memory()
+        th = torch.zeros(args.steps, 3, dtype=torch.float64).pin_memory()
+        xo = torch.zeros(3, n, dtype=torch.float64).pin_memory()
+        vo = torch.zeros(3, n, dtype=torch.float64).pin_memory()
+        h2 = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+        md.md_set_state(h2, xh, vh)          # first use: allocations and page-in, untimed
+        md.md_build_neighbors(h2)
+        md.md_step(h2, 3, 1, th)
+        md.md_sync(h2)
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        md.md_set_state(h2, xh, vh)
+        md.md_build_neighbors(h2)
+        md.md_step(h2, args.steps, 1, th)
+        md.md_get_state(h2, xo, vo)
+        t_e2e = time.perf_counter() - t0
+        t_e2e = barrier_max(t_e2e, world)
+        thermo = th.numpy()
+        E = thermo[:, 0] + thermo[:, 1]
+        extras["e2e"] = {"value": world * n * args.steps / t_e2e, "unit": UNIT,
+                         "h2d_bytes_per_step": 2 * 3 * n * 8 / args.steps,
+                         "d2h_bytes_per_step": (2 * 3 * n * 8 + 3 * 8 * args.steps) / args.steps,
+                         "includes": "set_state from pinned host, list build, K steps with (U,K,W) "
+                                     "every step, get_state to pinned host"}
+        extras["nve"] = {"steps": args.steps, "E0_per_particle": float(E[0] / n),
+                         "rel_drift": float((E[-1] - E[0]) / abs(E[0])),
+                         "max_rel_dev": float(np.max(np.abs(E - E[0])) / abs(E[0]))}
+        h2.destroy()
+
+        # ---- the plain FP64 path on the same input
+        k64 = max(5, min(args.steps, 20))
+        h3 = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP64)
+        md.md_set_state(h3, xt, vt)
+        md.md_build_neighbors(h3)
+        md.md_step(h3, 3)
+        md.md_sync(h3)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        md.md_step(h3, k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        h3.destroy()
+        v64 = n * k64 / (ms64 * 1e-3)
+        extras["fp64"] = {"value": world * v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                          "speedup_fp32_fixed_over_fp64": (value / world) / v64}
+
+        if world == 1 and rank == 0:
+            import oracle
+            # ---- force error of the FP32 path on a perturbed lattice of the same size
+            xp, vp, _ = inputs.perturbed_lattice(args.ncell, rho=RHO, T=T0, seed=5, amp=0.1)
+            h4 = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+            md.md_set_state(h4, torch.tensor(xp.T.copy(), device=dev), torch.tensor(vp.T.copy(), device=dev))
+            md.md_build_neighbors(h4)
+            f = torch.zeros(3, n, dtype=torch.float64, device=dev)
+            md.md_compute_forces(h4, f, None)
+            md.md_sync(h4)
+            h4.destroy()
+            idx = np.random.default_rng(9).choice(n, 256, replace=False)
+            Fo, _, _ = oracle.forces_sample(oracle.System(n, box, rc=RC), xp, idx)
+            Fg = f.cpu().numpy().T[idx]
+            mag = np.linalg.norm(Fo, axis=1)
+            rms = float(np.sqrt(np.mean(mag ** 2)))
+            extras["force_error"] = {"sample": 256, "max_rel": float(np.max(np.linalg.norm(Fg - Fo, axis=1) /
+                                                                           np.maximum(mag, rms))),
+                                     "input": "fcc lattice with uniform +-0.1 sigma displacements"}
+            extras["cpu_baseline"] = cpu_baseline(x, box)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+fixed64 (f64 integration)",
+                "data": "synthetic",
+                "config": {"workload": f"LJ fluid N={n} per GPU (fcc {args.ncell}^3 x 4), rho={RHO}, T*={T0}, "
+                                       f"rc={RC} shifted, skin={SKIN}, dt={DT}, NVE, FP32 pairs + 64-bit fixed-point "
+                                       f"sums", "particles_per_gpu": n,
+                           "parallelism": "replicas only" if world > 1 else "1 GPU",
+                           "l2": "working set larger than L2 (positions, velocities and the Verlet list: "
+                                 f"~{(n * (FORCE_FIXED_BYTES + list_bytes)) / 1e6:.0f} MB touched per step)"},
+                "roofline": roofline,
+                "gpu_launches": 1 + 10 * args.steps,
+                "rebuilds": st1["rebuilds"] - st0["rebuilds"],
+                "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / args.steps,
+                                         "force_integrate": sect_ms[md.MD_SECT_FORCE] / args.steps,
+                                         "other": sect_ms[md.MD_SECT_OTHER] / args.steps},
+                "mean_list_len": mean_nn,
+                "clocks": ck,
+                "csrc_sha": digest}
+        line.update(extras)
+        if "e2e" not in line:
+            line["e2e"] = None
+        print(json.dumps(line), flush=True)
+    h.destroy()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -150,6 +150,23 @@ md_status md_sync(md_handle *h, void *stream);
 /* Counters and latched errors; synchronises the device. */
 md_status md_get_stats(md_handle *h, md_stats *out);
 
+/* Section timers.  Sec. 4 of the paper splits the elapsed time of the
+ * integrator loop into sections (Pair / Neigh / Integrate ...); here the
+ * sections are the device-side cell sort + Verlet-list build chain
+ * (MD_SECT_NEIGH, timed every step, whether or not it rebuilt), the fused
+ * pair-force + velocity-Verlet kernel (MD_SECT_FORCE), and everything else in
+ * md_step (MD_SECT_OTHER: the first half kick of a call, a force evaluation
+ * when none is stored).  Timing uses CUDA events on the caller's stream. */
+enum { MD_SECT_NEIGH = 0, MD_SECT_FORCE = 1, MD_SECT_OTHER = 2, MD_NSECT = 3 };
+
+/* Enable (1) or disable (0) the section timers; enabling clears them. */
+md_status md_set_timing(md_handle *h, int32_t enable);
+
+/* Accumulated milliseconds and counts per section since md_set_timing(h, 1):
+ * ms[MD_NSECT], counts[MD_NSECT] (host arrays, either may be NULL).
+ * Synchronises the device. */
+md_status md_get_timing(md_handle *h, double *ms, int64_t *counts);
+
 /* Text of the last error on this handle ("" if none).  Valid until the next call. */
 const char *md_last_error(const md_handle *h);
 

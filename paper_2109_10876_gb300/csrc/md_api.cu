@@ -33,6 +33,13 @@ struct md_handle {
     long long thermo_cap = 0;
     unsigned long long *d_count = nullptr;
     std::string err;
+    // section timers: event pairs recorded in md_step, resolved in md_get_timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;   // (section, (start, stop))
+    double sect_ms[MD_NSECT] = {0, 0, 0};
+    long long sect_n[MD_NSECT] = {0, 0, 0};
 };
 
 namespace {
@@ -120,6 +127,45 @@ md_status ensure_thermo(md_handle *h, long long count)
     if (!h->thermo_stage) return fail(h, MD_ERR_CUDA, "cannot allocate thermo buffer");
     h->thermo_cap = count;
     return MD_OK;
+}
+
+cudaEvent_t next_event(md_handle *h)
+{
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+// record a timing mark on the stream; returns its pool index (or -1)
+long long mark(md_handle *h, cudaStream_t st)
+{
+    if (!h->timing) return -1;
+    cudaEvent_t e = next_event(h);
+    if (!e) return -1;
+    cudaEventRecord(e, st);
+    return (long long)h->ev_used - 1;
+}
+
+void section(md_handle *h, int sect, long long a, long long b)
+{
+    if (a >= 0 && b >= 0) h->ev_marks.push_back({sect, {(size_t)a, (size_t)b}});
+}
+
+// fold recorded marks into the accumulated section times (events complete)
+void resolve_timing(md_handle *h)
+{
+    for (auto &m : h->ev_marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[m.second.first], h->ev_pool[m.second.second]) == cudaSuccess) {
+            h->sect_ms[m.first] += ms;
+            h->sect_n[m.first] += 1;
+        }
+    }
+    h->ev_marks.clear();
+    h->ev_used = 0;
 }
 
 md_status sync_and_check(md_handle *h, cudaStream_t st)
@@ -378,6 +424,7 @@ void md_destroy(md_handle *h)
     if (!h) return;
     cudaDeviceSynchronize();
     for (void *q : h->allocs) cudaFree(q);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
 }
 
@@ -487,16 +534,24 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
     const long long nrec = thermo_every > 0 ? nsteps / thermo_every : 0;
     if (nrec > 0 && ensure_thermo(h, nrec * 3 * nrep) != MD_OK) return MD_ERR_CUDA;
     Bufs b = h->b;
+    if (h->timing && h->ev_marks.size() > 100000) resolve_timing(h);   // bounded event pool
+    long long t0 = mark(h, st);
     if (!h->F_valid) {
         mdk::launch_rebuild_chain(b, st);
         mdk::launch_force(b, h->precision, mdk::kModeStore, false, st);
     }
     mdk::launch_kick_drift(b, st);
+    section(h, MD_SECT_OTHER, t0, mark(h, st));
     for (int t = 1; t <= nsteps; ++t) {
         const bool rec = thermo_every > 0 && (t % thermo_every) == 0;
         b.thermo = rec ? h->thermo_stage + (long long)(t / thermo_every - 1) * 3 * nrep : nullptr;
+        long long a = mark(h, st);
         mdk::launch_rebuild_chain(b, st);
+        long long m = mark(h, st);
         mdk::launch_force(b, h->precision, t < nsteps ? mdk::kModeFused : mdk::kModeFinal, rec, st);
+        long long e = mark(h, st);
+        section(h, MD_SECT_NEIGH, a, m);
+        section(h, t < nsteps ? MD_SECT_FORCE : MD_SECT_OTHER, m, e);
     }
     if (!cuda_ok(h, cudaGetLastError(), "step launch")) return MD_ERR_CUDA;
     h->F_valid = true;
@@ -557,6 +612,29 @@ md_status md_get_stats(md_handle *h, md_stats *out)
     out->n_replicas = h->b.nrep;
     out->n_particles = h->N;
     return status_of(h, c.err);
+}
+
+md_status md_set_timing(md_handle *h, int32_t enable)
+{
+    if (!h) return MD_ERR_ARG;
+    if (!cuda_ok(h, cudaDeviceSynchronize(), "device synchronize")) return MD_ERR_CUDA;
+    h->timing = enable != 0;
+    h->ev_marks.clear();
+    h->ev_used = 0;
+    for (int k = 0; k < MD_NSECT; ++k) { h->sect_ms[k] = 0; h->sect_n[k] = 0; }
+    return MD_OK;
+}
+
+md_status md_get_timing(md_handle *h, double *ms, int64_t *counts)
+{
+    if (!h) return MD_ERR_ARG;
+    if (!cuda_ok(h, cudaDeviceSynchronize(), "device synchronize")) return MD_ERR_CUDA;
+    resolve_timing(h);
+    for (int k = 0; k < MD_NSECT; ++k) {
+        if (ms) ms[k] = h->sect_ms[k];
+        if (counts) counts[k] = h->sect_n[k];
+    }
+    return MD_OK;
 }
 
 const char *md_last_error(const md_handle *h) { return h ? h->err.c_str() : "null handle"; }

@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_CUDA", -3: "MD_ERR_LIS
                 -4: "MD_ERR_NONFINITE", -5: "MD_ERR_BOND_BROKEN", -6: "MD_ERR_FIXED_OVERFLOW",
                 -7: "MD_ERR_TIMEOUT", -8: "MD_ERR_BOX_TOO_SMALL"}
 MD_LJ, MD_WCA = 0, 1
+MD_SECT_NEIGH, MD_SECT_FORCE, MD_SECT_OTHER, MD_NSECT = 0, 1, 2, 3
 MD_FP64, MD_FP32_FIXED = 0, 1
 
 
@@ -100,6 +101,10 @@ _lib.md_sync.restype = C.c_int
 _lib.md_sync.argtypes = [_H, _vp]
 _lib.md_get_stats.restype = C.c_int
 _lib.md_get_stats.argtypes = [_H, C.POINTER(md_stats)]
+_lib.md_set_timing.restype = C.c_int
+_lib.md_set_timing.argtypes = [_H, C.c_int32]
+_lib.md_get_timing.restype = C.c_int
+_lib.md_get_timing.argtypes = [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
 _lib.md_last_error.restype = C.c_char_p
 _lib.md_last_error.argtypes = [_H]
 
@@ -242,6 +247,18 @@ def md_get_stats(h):
     st = _lib.md_get_stats(h.ptr, C.byref(s))
     _check(h.ptr, st)
     return {f: (list(getattr(s, f)) if f == "ncell" else getattr(s, f)) for f, _ in md_stats._fields_}
+
+
+def md_set_timing(h, enable=True):
+    return _check(h.ptr, _lib.md_set_timing(h.ptr, 1 if enable else 0))
+
+
+def md_get_timing(h):
+    """(ms[MD_NSECT], counts[MD_NSECT]) accumulated since md_set_timing(h, True)."""
+    ms = (C.c_double * MD_NSECT)()
+    n = (C.c_int64 * MD_NSECT)()
+    _check(h.ptr, _lib.md_get_timing(h.ptr, ms, n))
+    return list(ms), list(n)
 
 
 def md_last_error(h):
