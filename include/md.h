@@ -167,6 +167,29 @@ md_status md_set_timing(md_handle *h, int32_t enable);
  * Synchronises the device. */
 md_status md_get_timing(md_handle *h, double *ms, int64_t *counts);
 
+/* Force evaluation that allocates nothing, for callers that cannot allocate
+ * device memory (code running while a stream is captured into a CUDA graph,
+ * where cudaMalloc is not allowed, or a host framework that owns all device
+ * memory).  The paper has no counterpart: it is a convenience of this library.
+ *
+ * Computes the same conservative pair forces as md_compute_forces (shifted LJ
+ * when shift != 0, r < rc strict, minimum image in the orthorhombic box, FP32
+ * pairs with 64-bit fixed-point sums or FP64), summed directly over all pairs
+ * without cells or Verlet lists (O(n^2)), for ONE system of n particles.
+ *   x      device, (3, n) FP64 positions      v     device, (3, n) or NULL (K = 0)
+ *   box    host, 3 edges, each >= 2 rc        f_out device, (3, n) FP64 forces
+ *   euw_out device, 3 FP64 (U, K, W) or NULL  err_msg/err_len optional host text buffer
+ * Limits: 1 <= n <= 524288 (the fixed scratch), else MD_ERR_ARG with a message.
+ * Scratch: a fixed 64 KB device array in the library, held by every GPU that
+ * loads it until the process exits; every call shares it, so calls that
+ * overlap on the GPU race.  Nothing is allocated or freed.  The first call on
+ * a device looks up the scratch address with that device current; make that
+ * first call before any stream capture.  Asynchronous on `stream`. */
+md_status md_compute_forces_noalloc(const double *x, const double *v, int64_t n, const double *box,
+                                    double eps, double sigma, double rc, int32_t shift, int32_t precision,
+                                    double mass, double *f_out, double *euw_out, char *err_msg,
+                                    int32_t err_len, void *stream);
+
 /* Text of the last error on this handle ("" if none).  Valid until the next call. */
 const char *md_last_error(const md_handle *h);
 

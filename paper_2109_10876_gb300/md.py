@@ -105,6 +105,10 @@ _lib.md_set_timing.restype = C.c_int
 _lib.md_set_timing.argtypes = [_H, C.c_int32]
 _lib.md_get_timing.restype = C.c_int
 _lib.md_get_timing.argtypes = [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+_lib.md_compute_forces_noalloc.restype = C.c_int
+_lib.md_compute_forces_noalloc.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_double), C.c_double, C.c_double,
+                                           C.c_double, C.c_int32, C.c_int32, C.c_double, _vp, _vp,
+                                           C.c_char_p, C.c_int32, _vp]
 _lib.md_last_error.restype = C.c_char_p
 _lib.md_last_error.argtypes = [_H]
 
@@ -259,6 +263,20 @@ def md_get_timing(h):
     n = (C.c_int64 * MD_NSECT)()
     _check(h.ptr, _lib.md_get_timing(h.ptr, ms, n))
     return list(ms), list(n)
+
+
+def md_compute_forces_noalloc(x, v, n, box, f_out, euw_out=None, eps=1.0, sigma=1.0, rc=2.5, shift=True,
+                              precision=MD_FP32_FIXED, mass=1.0, stream=None):
+    """md_compute_forces_noalloc: direct all-pairs forces for one system, no
+    allocation (x, v, f_out, euw_out are device arrays; box is 3 host values)."""
+    boxa = (C.c_double * 3)(*[float(t) for t in np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))])
+    buf = C.create_string_buffer(256)
+    st = _lib.md_compute_forces_noalloc(_ptr(x), _ptr(v), int(n), boxa, float(eps), float(sigma), float(rc),
+                                        1 if shift else 0, int(precision), float(mass), _ptr(f_out),
+                                        _ptr(euw_out), buf, 256, _stream(stream))
+    if st != MD_OK:
+        raise MDError(st, buf.value.decode())
+    return st
 
 
 def md_last_error(h):
