@@ -127,3 +127,113 @@ def _rsa(n, box, rng, rmin, lo, hi, existing=None):
         if tries > 200 * n + 100000:
             raise RuntimeError("random sequential placement did not converge")
     return np.array(pts).reshape(-1, 3)
+
+
+def rsa_fast(n, box, lo, hi, rmin, rng, existing=None, batch=20000):
+    """Random sequential placement, vectorised: uniform candidates in [lo, hi),
+    each kept if at least rmin (minimum image) from every point kept before it
+    (and from `existing`).  A grid of cell edge rmin / sqrt(3) holds at most one
+    point per cell, so a candidate is checked against the 5 x 5 x 5 cells
+    around it; conflicts inside a batch are resolved in candidate order."""
+    from scipy.spatial import cKDTree
+    box = np.asarray(box, dtype=np.float64)
+    lo, hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
+    # edge <= rmin / sqrt(3): two kept points never share a cell; edge >= rmin / 2:
+    # everything within rmin lies in the 5 x 5 x 5 cells around a point
+    ng = np.maximum(np.ceil(box / (rmin / math.sqrt(3.0))).astype(np.int64), 1)
+    edge = box / ng
+    if np.any(edge < 0.5 * rmin) and np.any(ng > 4):
+        raise ValueError("box too small for the placement grid")
+    grid = np.full(int(ng[0] * ng[1] * ng[2]), -1, dtype=np.int64)
+    pts = np.zeros((n + (0 if existing is None else len(existing)), 3))
+    m = 0
+
+    def cell_of(p):
+        c = np.floor(p / edge).astype(np.int64) % ng
+        return (c[:, 2] * ng[1] + c[:, 1]) * ng[0] + c[:, 0], c
+
+    if existing is not None and len(existing):
+        k, _ = cell_of(existing)
+        pts[:len(existing)] = existing
+        grid[k] = np.arange(len(existing))
+        m = len(existing)
+    start = m
+    offs = np.array([(a, b, c) for a in range(-2, 3) for b in range(-2, 3) for c in range(-2, 3)])
+    tries = 0
+    while m - start < n:
+        cand = lo + rng.uniform(0.0, 1.0, size=(batch, 3)) * (hi - lo)
+        cand = np.mod(cand, box)
+        _, cc = cell_of(cand)
+        nb = (cc[:, None, :] + offs[None, :, :]) % ng
+        nbk = (nb[..., 2] * ng[1] + nb[..., 1]) * ng[0] + nb[..., 0]
+        idx = grid[nbk]                                   # (batch, 125)
+        d = cand[:, None, :] - pts[np.maximum(idx, 0)]
+        d -= box * np.round(d / box)
+        close = (np.sum(d * d, axis=2) < rmin * rmin) & (idx >= 0)
+        ok = ~close.any(axis=1)
+        good = np.nonzero(ok)[0]
+        # conflicts among this batch's survivors: keep the earlier candidate
+        if len(good) > 1:
+            tree = cKDTree(cand[good], boxsize=box)
+            drop = np.zeros(len(good), dtype=bool)
+            for a, b in sorted(tree.query_pairs(rmin)):
+                if not drop[a]:
+                    drop[b] = True
+            good = good[~drop]
+        good = good[:n - (m - start)]
+        k, _ = cell_of(cand[good])
+        pts[m:m + len(good)] = cand[good]
+        grid[k] = np.arange(m, m + len(good))
+        m += len(good)
+        tries += batch
+        if tries > 400 * n + 10 * batch:
+            raise RuntimeError("random sequential placement did not converge")
+    return pts[start:m]
+
+
+def slab(n, rho_l=0.80, rho_v=0.02, T=0.8, seed=3, rmin=0.8):
+    """Liquid/vapour slab: a periodic box with Lz = 4 Lx = 4 Ly; liquid at rho_l
+    in the central quarter of z (z in [3 Lz / 8, 5 Lz / 8)), vapour at rho_v
+    elsewhere; positions by random sequential placement with minimum separation
+    rmin (liquid first, then vapour), Gaussian velocities at T.  The particle
+    numbers split as n_liq = round(n rho_l / 4 / (rho_l / 4 + 3 rho_v / 4))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    frac = 0.25 * rho_l / (0.25 * rho_l + 0.75 * rho_v)
+    lx = (n / (4.0 * (0.25 * rho_l + 0.75 * rho_v))) ** (1.0 / 3.0)
+    box = np.array([lx, lx, 4.0 * lx])
+    n_liq = int(round(n * frac))
+    liq = rsa_fast(n_liq, box, [0.0, 0.0, 1.5 * lx], [lx, lx, 2.5 * lx], rmin, rng)
+    # vapour: uniform in the two outer regions (total length 3 lx), placed against the liquid
+    vap = rsa_fast(n - n_liq, box, [0.0, 0.0, 2.5 * lx], [lx, lx, 5.5 * lx], rmin, rng, existing=liq)
+    x = wrap(np.concatenate([liq, vap]), box)
+    v = maxwell_velocities(n, T, seed + 17)
+    return x, v, box
+
+
+def chains(nchain, nbead, box, seed, bond=0.97, rmin=0.75):
+    """Linear chains grown as self-avoiding random walks: bond length `bond`,
+    no two beads closer than rmin (minimum image).  For the small, dilute test
+    systems; returns positions and the bond list (pairs of particle indices)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    box = np.asarray(box, dtype=np.float64)
+    pts, bonds = [], []
+    for c in range(nchain):
+        for k in range(nbead):
+            for _ in range(10000):
+                if k == 0:
+                    p = rng.uniform(0, 1, 3) * box
+                else:
+                    u = rng.normal(size=3)
+                    p = pts[-1] + bond * u / np.linalg.norm(u)
+                if not pts:
+                    break
+                d = np.array(pts) - p
+                d -= box * np.round(d / box)
+                if np.min(np.sum(d * d, axis=1)) >= rmin * rmin:
+                    break
+            else:
+                raise RuntimeError("chain growth failed")
+            if k > 0:
+                bonds.append((len(pts) - 1, len(pts)))
+            pts.append(p)
+    return wrap(np.array(pts), box), np.array(bonds, dtype=np.int32)
