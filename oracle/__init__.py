@@ -70,6 +70,14 @@ def lib():
                                         C.POINTER(C.c_uint32)]
         L.orc_langevin_uniforms.restype = None
         L.orc_langevin_uniforms.argtypes = [C.c_uint64, C.c_int64, C.c_int64, dp]
+        L.orc_hvp.restype = None
+        L.orc_hvp.argtypes = [sp, dp, dp, dp, dp, dp]
+        L.orc_loss_grad.restype = None
+        L.orc_loss_grad.argtypes = [sp, dp, dp, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp]
+        L.orc_vv_adjoint.restype = C.c_int
+        L.orc_vv_adjoint.argtypes = [sp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp, dp]
+        L.orc_set_rc_fixed.restype = None
+        L.orc_set_rc_fixed.argtypes = [C.c_int]
         L.orc_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -206,6 +214,36 @@ def langevin_uniforms(seed, pid, step):
     u = np.zeros(3)
     lib().orc_langevin_uniforms(int(seed), int(pid), int(step), _dp(u))
     return u
+
+
+def hvp(sysm, x, w):
+    """(J w) of the pair forces at x, and (sum_i w_i . dF_i/deps, sum_i w_i . dF_i/dsigma)."""
+    x = _f64(x, (sysm.n, 3))
+    w = _f64(w, (sysm.n, 3))
+    hv = np.zeros((sysm.n, 3))
+    pe, ps = C.c_double(), C.c_double()
+    s = sysm.c()
+    lib().orc_hvp(C.byref(s), _dp(x), _dp(w), _dp(hv), C.byref(pe), C.byref(ps))
+    return hv, pe.value, ps.value
+
+
+def vv_adjoint(sysm, x, v, nsteps, cU, cK, cW, rc_fixed=False):
+    """Adjoint of nsteps NVE velocity-Verlet steps for L = cU U + cK K + cW W at
+    the end.  Returns (euw_T, dL/deps, dL/dsigma, lx0, lv0).  By default r_cut
+    moves with sigma (sysm.rc is rc_over_sigma * sigma); rc_fixed=True holds it."""
+    lib().orc_set_rc_fixed(1 if rc_fixed else 0)
+    x = _f64(x, (sysm.n, 3))
+    v = _f64(v, (sysm.n, 3))
+    euw = np.zeros(3)
+    ge, gs = C.c_double(), C.c_double()
+    lx = np.zeros((sysm.n, 3))
+    lv = np.zeros((sysm.n, 3))
+    s = sysm.c()
+    rc = lib().orc_vv_adjoint(C.byref(s), _dp(x), _dp(v), int(nsteps), float(cU), float(cK), float(cW),
+                              _dp(euw), C.byref(ge), C.byref(gs), _dp(lx), _dp(lv))
+    if rc != 0:
+        raise RuntimeError(f"oracle vv_adjoint failed: {rc}")
+    return euw, ge.value, gs.value, lx, lv
 
 
 def num_threads():

@@ -363,3 +363,183 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Adjoint of velocity Verlet (NVE, pair potential only) for a loss    */
+/* L(U_T, K_T, W_T) of the final state, by reverse-mode differentiation */
+/* of the map of Fig. 1.  Written from the equations:                  */
+/*   pair force on i:  f_ij = g(r) d,  g = 24 eps [2 (s/r)^12 - (s/r)^6] / r^2 */
+/*   Jacobian block:   dF_i/dx_j = -(g I + (g'/r) d d^T)  (j != i)     */
+/*   parameter terms:  dF_i/d eps = F_i / eps,                          */
+/*                     dF_i/d sigma = sum_j (dg/d sigma) d              */
+/* with r_cut = rc_over_sigma * sigma moving with sigma (V shifted to  */
+/* zero at r_cut, so U and W have no boundary term in sigma); pairs     */
+/* that cross r_cut as sigma changes contribute delta terms that a      */
+/* pointwise derivative does not see.                                   */
+/* ------------------------------------------------------------------ */
+
+/* g(r), g'(r)/r and dg/dsigma for separation r^2 (r < rc). */
+static void lj_g_terms(double eps, double sigma, double r2, double *g, double *gpr, double *dgds)
+{
+    double s2 = sigma * sigma / r2;
+    double s6 = s2 * s2 * s2;
+    double s12 = s6 * s6;
+    *g = 24.0 * eps * (2.0 * s12 - s6) / r2;
+    *gpr = 24.0 * eps * (8.0 * s6 - 28.0 * s12) / (r2 * r2);
+    *dgds = 24.0 * eps * (24.0 * s12 - 6.0 * s6) / (sigma * r2);
+}
+
+/* (J w)_i for the pair forces at x, and the parameter projections
+ * pe = sum_i w_i . dF_i/deps and ps = sum_i w_i . dF_i/dsigma. */
+void orc_hvp(const orc_system *s, const double *x, const double *w, double *hv, double *pe, double *ps)
+{
+    int64_t n = s->n;
+    double rc2 = s->rc * s->rc;
+    double *pe_i = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *ps_i = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double acc[3] = {0, 0, 0}, F[3] = {0, 0, 0}, Fs[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            double r2 = min_image(&x[3 * i], &x[3 * j], s->box, d);
+            if (!(r2 < rc2)) continue;
+            double g, gpr, dgds;
+            lj_g_terms(s->eps, s->sigma, r2, &g, &gpr, &dgds);
+            double dw[3] = {w[3 * i] - w[3 * j], w[3 * i + 1] - w[3 * j + 1], w[3 * i + 2] - w[3 * j + 2]};
+            double ddw = d[0] * dw[0] + d[1] * dw[1] + d[2] * dw[2];
+            for (int k = 0; k < 3; ++k) {
+                acc[k] += g * dw[k] + gpr * d[k] * ddw;
+                F[k] += g * d[k];
+                Fs[k] += dgds * d[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) hv[3 * i + k] = acc[k];
+        pe_i[i] = (w[3 * i] * F[0] + w[3 * i + 1] * F[1] + w[3 * i + 2] * F[2]) / s->eps;
+        ps_i[i] = w[3 * i] * Fs[0] + w[3 * i + 1] * Fs[1] + w[3 * i + 2] * Fs[2];
+    }
+    double a = 0, b = 0;
+    for (int64_t i = 0; i < n; ++i) { a += pe_i[i]; b += ps_i[i]; }
+    free(pe_i);
+    free(ps_i);
+    *pe = a;
+    *ps = b;
+}
+
+/* Gradient of L = cU U + cK K + cW W at the final state (x, v):
+ *   lx = -cU F + cW dW/dx,  lv = cK m v,
+ *   g_eps = (cU U + cW W) / eps,
+ *   g_sigma = cU dU/dsigma + cW sum_pairs r^2 dg/dsigma, where dU/dsigma = W / sigma
+ *   when r_cut moves with sigma (the shifted energy is a function of r / sigma),
+ *   and W / sigma - n_pairs g(r_cut) r_cut^2 / sigma when r_cut is fixed (the
+ *   shift V(r_cut) then depends on sigma). */
+static int g_rc_fixed = 0;
+void orc_set_rc_fixed(int fixed) { g_rc_fixed = fixed; }
+
+void orc_loss_grad(const orc_system *s, const double *x, const double *v, double cU, double cK, double cW,
+                   double *lx, double *lv, double *g_eps, double *g_sig)
+{
+    int64_t n = s->n;
+    double rc2 = s->rc * s->rc;
+    double U = 0, W = 0, Ws = 0, npair = 0;
+    double *Ui = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *Pi = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *Wi = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *Wsi = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        double F[3] = {0, 0, 0}, dW[3] = {0, 0, 0}, u = 0, wv = 0, ws = 0, np_ = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            double r2 = min_image(&x[3 * i], &x[3 * j], s->box, d);
+            if (!(r2 < rc2)) continue;
+            double g, gpr, dgds;
+            lj_g_terms(s->eps, s->sigma, r2, &g, &gpr, &dgds);
+            double r = sqrt(r2);
+            double vp = orc_lj_energy(r, s->eps, s->sigma);
+            if (s->shift) vp -= orc_lj_energy(s->rc, s->eps, s->sigma);
+            for (int k = 0; k < 3; ++k) {
+                F[k] += g * d[k];
+                dW[k] += (2.0 * g + gpr * r2) * d[k];    /* d(g r^2)/dd = (2 g + g' r) d */
+            }
+            u += 0.5 * vp;
+            wv += 0.5 * g * r2;
+            ws += 0.5 * r2 * dgds;
+            np_ += 0.5;
+        }
+        for (int k = 0; k < 3; ++k) {
+            lx[3 * i + k] = -cU * F[k] + cW * dW[k];
+            lv[3 * i + k] = cK * s->mass * v[3 * i + k];
+        }
+        Ui[i] = u;
+        Wi[i] = wv;
+        Wsi[i] = ws;
+        Pi[i] = np_;
+    }
+    for (int64_t i = 0; i < n; ++i) { U += Ui[i]; W += Wi[i]; Ws += Wsi[i]; npair += Pi[i]; }
+    free(Pi);
+    free(Ui);
+    free(Wi);
+    free(Wsi);
+    double dUds = W / s->sigma;
+    if (g_rc_fixed && s->shift) {
+        double g, gpr, dgds;
+        lj_g_terms(s->eps, s->sigma, s->rc * s->rc, &g, &gpr, &dgds);
+        dUds -= npair * g * s->rc * s->rc / s->sigma;
+    }
+    *g_eps = (cU * U + cW * W) / s->eps;
+    *g_sig = cU * dUds + cW * Ws;
+}
+
+/* Reverse pass through nsteps NVE velocity-Verlet steps from (x0, v0):
+ * runs the forward (keeping every position), then the adjoint of each step
+ * (half kick, drift, half kick, in reverse).  Outputs the final (U, K, W),
+ * dL/deps, dL/dsigma, and the adjoints lx0, lv0 of the initial state. */
+int orc_vv_adjoint(const orc_system *s, const double *x0, const double *v0, int64_t nsteps,
+                   double cU, double cK, double cW, double *euw, double *g_eps, double *g_sig,
+                   double *lx0, double *lv0)
+{
+    int64_t n = s->n;
+    size_t sz = (size_t)(3 * n);
+    double *X = (double *)malloc(sizeof(double) * sz * (size_t)(nsteps + 1));
+    double *v = (double *)malloc(sizeof(double) * sz);
+    double *F = (double *)malloc(sizeof(double) * sz);
+    double *w = (double *)malloc(sizeof(double) * sz);
+    double *hv = (double *)malloc(sizeof(double) * sz);
+    if (!X || !v || !F || !w || !hv) { free(X); free(v); free(F); free(w); free(hv); return ORC_ERR_ARG; }
+    memcpy(X, x0, sizeof(double) * sz);
+    memcpy(v, v0, sizeof(double) * sz);
+    double h = 0.5 * s->dt / s->mass;
+    orc_forces(s, X, NULL, F, NULL);
+    for (int64_t t = 0; t < nsteps; ++t) {
+        double *xa = X + sz * (size_t)t, *xb = X + sz * (size_t)(t + 1);
+        for (size_t q = 0; q < sz; ++q) {
+            v[q] += h * F[q];
+            xb[q] = wrap(xa[q] + s->dt * v[q], s->box[q % 3]);
+        }
+        orc_forces(s, xb, NULL, F, NULL);
+        for (size_t q = 0; q < sz; ++q) v[q] += h * F[q];
+    }
+    double *xT = X + sz * (size_t)nsteps;
+    orc_forces(s, xT, v, F, euw);
+    double ge, gs;
+    double *lx = lx0, *lv = lv0;
+    orc_loss_grad(s, xT, v, cU, cK, cW, lx, lv, &ge, &gs);
+    for (int64_t t = nsteps; t >= 0 && nsteps > 0; --t) {
+        /* kick(s) at x_t: the first half kick of step t and the second of step t-1 */
+        double c = (t == nsteps || t == 0) ? h : 2.0 * h;
+        double pe, ps;
+        orc_hvp(s, X + sz * (size_t)t, lv, hv, &pe, &ps);
+        for (size_t q = 0; q < sz; ++q) lx[q] += c * hv[q];
+        ge += c * pe;
+        gs += c * ps;
+        if (t > 0)   /* drift of step t-1: x_t = x_{t-1} + dt v_half */
+            for (size_t q = 0; q < sz; ++q) lv[q] += s->dt * lx[q];
+    }
+    *g_eps = ge;
+    *g_sig = gs;
+    free(X); free(v); free(F); free(w); free(hv);
+    return ORC_OK;
+}

@@ -298,3 +298,73 @@ def test_langevin_uniforms_moments_and_thermostat_temperature():
     x, v, F, th = oracle.vv_run(s, x, v, 4000, thermo=True)
     T = 2 * th[1000:, 1] / (3 * n)
     assert T.mean() == pytest.approx(1.3, rel=0.06)
+
+
+# ------------------------------------------------------------------ adjoint pins
+def _loss(x, v, box, eps, sig, T, rc, cU, cK, cW):
+    n = len(x)
+    s = oracle.System(n, box, eps=eps, sigma=sig, rc=rc, dt=0.005)
+    x1, v1, _ = oracle.vv_run(s, x, v, T)
+    _, euw = oracle.forces(s, x1, v1)
+    return cU * euw[0] + cK * euw[1] + cW * euw[2]
+
+
+def test_hvp_is_derivative_of_forces():
+    """(J w) from the oracle equals the directional derivative of the forces,
+    F(x + h w) - F(x - h w) over 2h, and the parameter projections equal the
+    derivatives of w . F in eps and sigma (r_cut held fixed)."""
+    x, v, box = _liquid(ncell=3, seed=9, amp=0.1)
+    n = len(x)
+    rng = np.random.default_rng(10)
+    w = rng.normal(size=(n, 3))
+    s = oracle.System(n, box, rc=2.5)
+    hv, pe, ps = oracle.hvp(s, x, w)
+    h = 1e-6
+    Fp, _ = oracle.forces(s, x + h * w)
+    Fm, _ = oracle.forces(s, x - h * w)
+    np.testing.assert_allclose(hv, (Fp - Fm) / (2 * h), rtol=1e-6, atol=1e-5)
+    F0, _ = oracle.forces(s, x)
+    Fe, _ = oracle.forces(oracle.System(n, box, eps=1 + h, rc=2.5), x)
+    assert pe == pytest.approx(np.sum(w * (Fe - F0)) / h, rel=1e-6)
+    Fsp, _ = oracle.forces(oracle.System(n, box, sigma=1 + h, rc=2.5), x)
+    Fsm, _ = oracle.forces(oracle.System(n, box, sigma=1 - h, rc=2.5), x)
+    assert ps == pytest.approx(np.sum(w * (Fsp - Fsm)) / (2 * h), rel=1e-6)
+
+
+@pytest.mark.parametrize("T", [0, 1, 5])
+def test_adjoint_matches_central_differences(T):
+    """d L / d(eps, sigma) by the reverse pass equals central differences of
+    the forward (h = 1e-4) for L = U/N + (2K + W)/(3V) after T steps.  For
+    sigma the cutoff is held fixed: a cutoff that moves with sigma sweeps pairs
+    across r_cut, where the virial jumps, which no pointwise derivative sees."""
+    x, v, box = _liquid(ncell=3, seed=5, amp=0.1)
+    n = len(x)
+    V = float(np.prod(box))
+    c = (1.0 / n, 2.0 / (3 * V), 1.0 / (3 * V))
+    s = oracle.System(n, box, rc=2.5, dt=0.005)
+    h = 1e-4
+    _, ge, _, _, _ = oracle.vv_adjoint(s, x, v, T, *c)
+    fe = (_loss(x, v, box, 1 + h, 1, T, 2.5 * (1 + 0), *c) - _loss(x, v, box, 1 - h, 1, T, 2.5, *c)) / (2 * h)
+    assert ge == pytest.approx(fe, rel=1e-6)
+    _, _, gs, _, _ = oracle.vv_adjoint(s, x, v, T, *c, rc_fixed=True)
+    fs = (_loss(x, v, box, 1, 1 + h, T, 2.5, *c) - _loss(x, v, box, 1, 1 - h, T, 2.5, *c)) / (2 * h)
+    assert gs == pytest.approx(fs, rel=1e-5)
+
+
+def test_adjoint_initial_state_gradient():
+    """The adjoint of the initial positions and velocities is the gradient of
+    the loss after T steps (central differences along random directions)."""
+    x, v, box = _liquid(ncell=3, seed=6, amp=0.1)
+    n = len(x)
+    V = float(np.prod(box))
+    c = (1.0 / n, 2.0 / (3 * V), 1.0 / (3 * V))
+    s = oracle.System(n, box, rc=2.5, dt=0.005)
+    _, _, _, lx, lv = oracle.vv_adjoint(s, x, v, 4, *c)
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    for _ in range(2):
+        dx, dv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+        fx = (_loss(x + h * dx, v, box, 1, 1, 4, 2.5, *c) - _loss(x - h * dx, v, box, 1, 1, 4, 2.5, *c)) / (2 * h)
+        fv = (_loss(x, v + h * dv, box, 1, 1, 4, 2.5, *c) - _loss(x, v - h * dv, box, 1, 1, 4, 2.5, *c)) / (2 * h)
+        assert np.sum(lx * dx) == pytest.approx(fx, rel=1e-5)
+        assert np.sum(lv * dv) == pytest.approx(fv, rel=1e-5)
