@@ -138,6 +138,25 @@ md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *
  * FP64 each.  Asynchronous; device errors are latched. */
 md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream);
 
+/* Differentiable run (reverse-mode differentiation of the velocity-Verlet map
+ * of Fig. 1; the paper itself has no gradients).  Advance nsteps NVE steps from
+ * the current state, keeping (x, v) every ckpt_every steps in device memory the
+ * handle owns, and write (U, K, W) per replica of the final state to euw_out
+ * (3 * n_replicas FP64, host or device, may be NULL).  Pair potentials only:
+ * returns MD_ERR_ARG for handles with FENE bonds or a thermostat.
+ * Synchronises `stream`. */
+md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *euw_out, void *stream);
+
+/* Reverse pass of the last md_forward for a loss L(U, K, W) of its final state.
+ * dL_deuw: (dL/dU, dL/dK, dL/dW) per replica, 3 * n_replicas FP64, host or
+ * device.  Writes dL/deps and dL/dsigma per replica (n_replicas FP64 each, host
+ * or device): the derivative of the smooth flow, with r_cut = rc_over_sigma *
+ * sigma moving with sigma (pairs crossing r_cut contribute jump terms that are
+ * not included).  Recomputes each segment from its checkpoint; Hessian-vector
+ * products and all adjoint sums in FP64.  Leaves the handle at the final state
+ * of the recorded run (step counter and stats reset).  Synchronises `stream`. */
+md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, double *dL_dsigma, void *stream);
+
 /* Export the current Verlet pair set as pairs (i, j), i < j, in the caller's
  * particle numbering, in no particular order.  Writes at most `capacity` pairs
  * (2 * capacity int32) to pairs_out and the total count to *n_out (host).

@@ -1,0 +1,53 @@
+"""torch.autograd face of the library's reverse pass (md_forward / md_backward).
+
+`ensemble_euw(eps, sigma, spec)` runs a differentiable velocity-Verlet
+trajectory of every replica (all in one handle) and returns the final
+(U, K, W) per replica as a (R, 3) tensor whose backward calls md_backward:
+d(loss)/d(eps, sigma) per replica comes from the library's FP64 adjoint, not
+from autograd through the steps.  Argument marshalling only.
+"""
+import numpy as np
+import torch
+
+from . import md
+
+
+class _Run(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, eps, sigma, spec):
+        h = md.md_create(spec["sizes"], spec["box"], eps=eps.detach().cpu().numpy(),
+                         sigma=sigma.detach().cpu().numpy(), rc_over_sigma=spec.get("rc_over_sigma", 2.5),
+                         skin=spec.get("skin", 0.3), dt=spec.get("dt", 0.005),
+                         precision=spec.get("precision", md.MD_FP32_FIXED))
+        md.md_set_state(h, spec["x"], spec["v"])
+        md.md_build_neighbors(h)
+        euw = torch.zeros(len(spec["sizes"]), 3, dtype=torch.float64)
+        md.md_forward(h, spec["nsteps"], spec.get("ckpt_every", 20), euw)
+        ctx.h = h
+        return euw
+
+    @staticmethod
+    def backward(ctx, g_euw):
+        R = g_euw.shape[0]
+        ge = torch.zeros(R, dtype=torch.float64)
+        gs = torch.zeros(R, dtype=torch.float64)
+        md.md_backward(ctx.h, g_euw.detach().to(torch.float64).contiguous().cpu(), ge, gs)
+        ctx.h.destroy()
+        return ge, gs, None
+
+
+def ensemble_euw(eps, sigma, spec):
+    """(U, K, W) per replica after spec['nsteps'] steps, differentiable in eps, sigma.
+
+    spec: sizes (per replica), box ((R, 3) array), x, v ((3, N) device tensors,
+    replicas concatenated), nsteps, ckpt_every, and optionally rc_over_sigma,
+    skin, dt, precision."""
+    return _Run.apply(eps, sigma, spec)
+
+
+def mean_energy_plus_pressure(euw, sizes, boxes):
+    """Loss per replica U/N + (2K + W) / (3V): the mean potential energy plus the
+    virial pressure of the final state."""
+    n = torch.as_tensor(np.asarray(sizes, dtype=np.float64))
+    vol = torch.as_tensor(np.prod(np.asarray(boxes, dtype=np.float64), axis=1))
+    return euw[:, 0] / n + (2.0 * euw[:, 1] + euw[:, 2]) / (3.0 * vol)

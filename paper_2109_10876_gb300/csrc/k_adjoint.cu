@@ -1,0 +1,259 @@
+// Adjoint kernels for reverse-mode differentiation through velocity Verlet
+// (NVE, pair potential of Eq. 2; arXiv:2109.10876 Fig. 1 gives the map being
+// differentiated).  For a loss L(U, K, W) of the final state the reverse pass
+// needs, at recorded positions x:
+//   the Hessian-vector product of the pair forces, (J w)_i = sum_j
+//     [g (w_i - w_j) + (g'/r) d (d . (w_i - w_j))],  f_ij = g(r) d,
+//   the parameter projections sum_i w_i . dF_i/deps = sum_i w_i . F_i / eps and
+//     sum_i w_i . dF_i/dsigma = sum_i w_i . sum_j (dg/dsigma) d,
+// and, at the final state, F, dW/dx, U, W and sum_pairs r^2 dg/dsigma.
+// All in FP64, over the Verlet lists of the forward machinery (tiles, halo in
+// shared memory).  Vectors w, J w and the adjoints live in the caller's
+// particle order; kernels map through the particle id in pos.w.
+#include <algorithm>
+
+#include "md_internal.cuh"
+
+namespace mdk {
+
+__device__ __noinline__ double adj_r2_exact(const double *x, long long S, long long i, long long j, const double *L)
+{
+    double d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double t = __dsub_rn(x[k * S + i], x[k * S + j]);
+        const double q = rint(__ddiv_rn(t, L[k]));
+        d[k] = __dsub_rn(t, __dmul_rn(L[k], q));
+    }
+    return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+}
+
+__device__ __forceinline__ int adj_halo_slot(const Piece *pc, int np, int h)
+{
+    int q = 0;
+    while (q + 1 < np && h >= pc[q + 1].hoff) ++q;
+    return pc[q].slot0 + (h - pc[q].hoff);
+}
+
+// Last block: per-replica sums of the 4 per-tile partials, in tile order,
+// added into acc[4 * r + k] with weight `scale`.
+__device__ void adj_reduce(const Bufs &b, double scale, double *acc)
+{
+    __shared__ double red[kBlock][4];
+    for (int r = 0; r < b.nrep; ++r) {
+        double a[4] = {0, 0, 0, 0};
+        for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x)
+            for (int k = 0; k < 4; ++k) a[k] += b.partial[4 * q + k];
+        for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = a[k];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s)
+                for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 4; ++k) acc[4 * r + k] += scale * red[0][k];
+        __syncthreads();
+    }
+}
+
+// MODE 0 (HVP): hv = J w at the current positions; partials (w.F/eps, w.dF/dsigma).
+// MODE 1 (LOSS): lx = -cU F + cW dW/dx, lv = cK m v; partials (U, W, sum r^2 dg/dsigma).
+// coef: per replica (cU, cK, cW, -) for LOSS; the partials are added into
+// acc (4 per replica) with weight `scale`.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double *out0, double *out1,
+                                                const double *coef, double scale, double *acc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Piece pc[kMaxPieces + 1];
+    __shared__ Tile tl;
+    __shared__ int s_tile, s_np;
+    __shared__ double sm4[kBlock / 32][4];
+    __shared__ bool last;
+    if (b.ctl->err) return;
+    const int cur = b.ctl->cur;
+    const double *X = b.x[cur];
+    const uint4 *P = b.pos[cur];
+    double *hx = reinterpret_cast<double *>(smem_raw);
+    double *hy = hx + b.hcap, *hz = hy + b.hcap;
+    double *hw = hz + b.hcap;                     // 3 * hcap: w of the halo (MODE 0)
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= b.ctl->ntiles) break;
+        load_tile(b, t, tl, pc, s_np);
+        __syncthreads();
+        const Replica &R = b.rep[tl.rep];
+        const int np = s_np;
+        const int Pt = tl.s1 - tl.s0;
+        stage_halo<double>(pc, np, [&](int h, int j) {
+            hx[h] = X[j];
+            hy[h] = X[b.S + j];
+            hz[h] = X[2 * b.S + j];
+            if (MODE == 0) {
+                const int id = (int)P[j].w;
+                hw[3 * h + 0] = w[id];
+                hw[3 * h + 1] = w[b.N + id];
+                hw[3 * h + 2] = w[2 * b.N + id];
+            }
+        });
+        __syncthreads();
+        const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
+        const double h0 = 0.5 * L0, h1 = 0.5 * L1, h2 = 0.5 * L2;
+        const double eps = R.eps, sig = R.sigma, sig2 = sig * sig, rc2 = R.rc2;
+        const double band = 1e-12 * rc2;
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+            const int id = (int)P[i].w;
+            const int n = min(b.nn[i], b.K);
+            const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
+            const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
+            double wi[3] = {0, 0, 0};
+            if (MODE == 0) { wi[0] = w[id]; wi[1] = w[b.N + id]; wi[2] = w[2 * b.N + id]; }
+            double acc3[3] = {0, 0, 0}, F[3] = {0, 0, 0}, Fs[3] = {0, 0, 0};
+            double u = 0.0, wv = 0.0, ws = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const int h = __ldg(nb + (long long)k * Pt);
+                double dx = xi0 - hx[h], dy = xi1 - hy[h], dz = xi2 - hz[h];
+                dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
+                dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
+                dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < rc2 + band)) continue;
+                if (!(r2 < rc2 - band) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < rc2)) continue;
+                const double s2 = sig2 / r2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+                const double g = 24.0 * eps * (2.0 * s12 - s6) / r2;
+                const double gpr = 24.0 * eps * (8.0 * s6 - 28.0 * s12) / (r2 * r2);
+                const double dgds = 24.0 * eps * (24.0 * s12 - 6.0 * s6) / (sig * r2);
+                const double d[3] = {dx, dy, dz};
+                if (MODE == 0) {
+                    const double dw[3] = {wi[0] - hw[3 * h], wi[1] - hw[3 * h + 1], wi[2] - hw[3 * h + 2]};
+                    const double ddw = dx * dw[0] + dy * dw[1] + dz * dw[2];
+                    for (int q = 0; q < 3; ++q) {
+                        acc3[q] += g * dw[q] + gpr * d[q] * ddw;
+                        F[q] += g * d[q];
+                        Fs[q] += dgds * d[q];
+                    }
+                } else {
+                    for (int q = 0; q < 3; ++q) {
+                        F[q] += g * d[q];
+                        acc3[q] += (2.0 * g + gpr * r2) * d[q];      // dW/dx_i
+                    }
+                    u += 0.5 * (4.0 * eps * (s12 - s6) - R.vshift);
+                    wv += 0.5 * g * r2;
+                    ws += 0.5 * r2 * dgds;
+                }
+            }
+            if (MODE == 0) {
+                for (int q = 0; q < 3; ++q) out0[q * b.N + id] = acc3[q];
+                p0 += (wi[0] * F[0] + wi[1] * F[1] + wi[2] * F[2]) / eps;
+                p1 += wi[0] * Fs[0] + wi[1] * Fs[1] + wi[2] * Fs[2];
+            } else {
+                const double cU = coef[4 * tl.rep], cK = coef[4 * tl.rep + 1], cW = coef[4 * tl.rep + 2];
+                for (int q = 0; q < 3; ++q) {
+                    out0[q * b.N + id] = -cU * F[q] + cW * acc3[q];
+                    out1[q * b.N + id] = cK * b.mass * b.v[cur][q * b.S + i];
+                }
+                p0 += u;
+                p1 += wv;
+                p2 += ws;
+            }
+        }
+        // per-tile partials in a fixed order
+        for (int o = 16; o > 0; o >>= 1) {
+            p0 += __shfl_down_sync(0xffffffffu, p0, o);
+            p1 += __shfl_down_sync(0xffffffffu, p1, o);
+            p2 += __shfl_down_sync(0xffffffffu, p2, o);
+        }
+        if ((threadIdx.x & 31) == 0) { sm4[threadIdx.x >> 5][0] = p0; sm4[threadIdx.x >> 5][1] = p1; sm4[threadIdx.x >> 5][2] = p2; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, c = 0, d = 0;
+            for (int q = 0; q < kBlock / 32; ++q) { a += sm4[q][0]; c += sm4[q][1]; d += sm4[q][2]; }
+            b.partial[4 * t + 0] = a;
+            b.partial[4 * t + 1] = c;
+            b.partial[4 * t + 2] = d;
+            b.partial[4 * t + 3] = 0.0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&b.ctl->done_force, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    adj_reduce(b, scale, acc);
+    if (threadIdx.x == 0) {
+        b.ctl->tile_next = 0u;
+        b.ctl->done_force = 0u;
+    }
+}
+
+// lx += c hv; then lv += dt lx (caller order, 3 N values each).
+__global__ void k_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n3; q += (long long)gridDim.x * blockDim.x) {
+        const double x = lx[q] + c * hv[q];
+        lx[q] = x;
+        lv[q] += dt * x;
+    }
+}
+
+// Explicit parameter terms of the loss from the per-replica sums (U, W, Ws):
+// g_eps += (cU U + cW W) / eps, g_sigma += cU W / sigma + cW Ws (r_cut moves
+// with sigma, so dU/dsigma = W / sigma); g holds (g_eps, g_sigma, -, -) per replica.
+__global__ void k_adj_finish_loss(Bufs b, const double *sums, const double *coef, double *g)
+{
+    for (int r = 0; r < b.nrep; ++r) {
+        const double U = sums[4 * r], W = sums[4 * r + 1], Ws = sums[4 * r + 2];
+        const double cU = coef[4 * r], cW = coef[4 * r + 2];
+        g[4 * r + 0] += (cU * U + cW * W) / b.rep[r].eps;
+        g[4 * r + 1] += cU * W / b.rep[r].sigma + cW * Ws;
+    }
+}
+
+static int adj_grid(const void *fn, size_t smem)
+{
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBlock, smem);
+    return (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
+}
+
+// hv = J w at the current state; g[4 r + k] += scale * (w.F/eps, w.dF/dsigma)_r.
+void launch_adj_hvp(const Bufs &b, const double *w, double *hv, double scale, double *g, cudaStream_t st)
+{
+    const size_t smem = (size_t)b.hcap * 6 * sizeof(double);
+    static int grid = 0;
+    static size_t gs = 0;
+    if (grid == 0 || gs != smem) { grid = adj_grid((const void *)k_adj<0>, smem); gs = smem; }
+    k_adj<0><<<grid, kBlock, smem, st>>>(b, w, hv, nullptr, nullptr, scale, g);
+}
+
+// lx, lv of the loss at the current state; sums[4 r + k] += (U, W, Ws)_r.
+void launch_adj_loss(const Bufs &b, const double *coef, double *lx, double *lv, double *sums, cudaStream_t st)
+{
+    const size_t smem = (size_t)b.hcap * 6 * sizeof(double);
+    static int grid = 0;
+    static size_t gs = 0;
+    if (grid == 0 || gs != smem) { grid = adj_grid((const void *)k_adj<1>, smem); gs = smem; }
+    k_adj<1><<<grid, kBlock, smem, st>>>(b, nullptr, lx, lv, coef, 1.0, sums);
+}
+
+void launch_adj_finish_loss(const Bufs &b, const double *sums, const double *coef, double *g, cudaStream_t st)
+{
+    k_adj_finish_loss<<<1, 1, 0, st>>>(b, sums, coef, g);
+}
+
+void launch_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt, cudaStream_t st)
+{
+    k_adj_update<<<(unsigned)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, st>>>(n3, lx, lv, hv, c, dt);
+}
+
+}  // namespace mdk

@@ -40,6 +40,16 @@ struct md_handle {
     std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;   // (section, (start, stop))
     double sect_ms[MD_NSECT] = {0, 0, 0};
     long long sect_n[MD_NSECT] = {0, 0, 0};
+    // recorded differentiable run (md_forward) for md_backward
+    bool ad_ready = false;
+    int ad_T = 0, ad_k = 1;
+    double *ad_ck = nullptr;        // checkpoints: (x, v) in caller order, 6 N each
+    long long ad_ck_cap = 0;        // checkpoints the buffer holds
+    double *ad_fin = nullptr;       // final (x, v), 6 N
+    double *ad_work = nullptr;      // lx, lv, hv, zero v: 4 x 3 N
+    double *ad_seg = nullptr;       // positions of one segment: (k + 1) x 3 N
+    long long ad_seg_cap = 0;
+    double *ad_small = nullptr;     // coef (4 nrep), g (4 nrep), sums (4 nrep)
 };
 
 namespace {
@@ -127,6 +137,15 @@ md_status ensure_thermo(md_handle *h, long long count)
     if (!h->thermo_stage) return fail(h, MD_ERR_CUDA, "cannot allocate thermo buffer");
     h->thermo_cap = count;
     return MD_OK;
+}
+
+double *grow(md_handle *h, double *old, size_t count)
+{
+    if (old) {
+        for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+            if (*it == old) { cudaFree(*it); h->allocs.erase(it); break; }
+    }
+    return dalloc<double>(h, count);
 }
 
 cudaEvent_t next_event(md_handle *h)
@@ -612,6 +631,126 @@ md_status md_get_stats(md_handle *h, md_stats *out)
     out->n_replicas = h->b.nrep;
     out->n_particles = h->N;
     return status_of(h, c.err);
+}
+
+md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *euw_out, void *stream)
+{
+    if (!h || nsteps < 0 || ckpt_every < 1) return fail(h, MD_ERR_ARG, "md_forward: bad arguments");
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_forward before md_set_state");
+    if (h->b.has_bonds || h->b.langevin)
+        return fail(h, MD_ERR_ARG, "md_forward: the adjoint covers NVE pair potentials only (no bonds, no thermostat)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n6 = 6LL * h->N;
+    const long long nck = nsteps / ckpt_every + 1;
+    if (h->ad_ck_cap < nck) {
+        h->ad_ck = grow(h, h->ad_ck, (size_t)(nck * n6));
+        if (!h->ad_ck) return fail(h, MD_ERR_CUDA, "cannot allocate checkpoints");
+        h->ad_ck_cap = nck;
+    }
+    if (!h->ad_fin && !(h->ad_fin = dalloc<double>(h, (size_t)n6))) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    h->ad_ready = false;
+    for (long long c = 0; c < nck; ++c) {
+        double *ck = h->ad_ck + c * n6;
+        mdk::launch_get_state(h->b, ck, ck + 3 * h->N, st);
+        const long long rest = nsteps - c * ckpt_every;
+        const int run = (int)std::min<long long>(ckpt_every, rest);
+        if (run > 0) {
+            md_status s = md_step(h, run, 0, nullptr, stream);
+            if (s != MD_OK) return s;
+        }
+    }
+    mdk::launch_get_state(h->b, h->ad_fin, h->ad_fin + 3 * h->N, st);
+    if (euw_out) {
+        md_status s = md_compute_forces(h, nullptr, euw_out, stream);
+        if (s != MD_OK) return s;
+    }
+    h->ad_T = nsteps;
+    h->ad_k = ckpt_every;
+    md_status s = sync_and_check(h, st);
+    if (s == MD_OK) h->ad_ready = true;
+    return s;
+}
+
+// set the handle's state from caller-order device arrays and build its lists
+static md_status adj_load(md_handle *h, const double *x, const double *v, cudaStream_t st)
+{
+    md_status s = md_set_state(h, x, v, st);
+    if (s != MD_OK) return s;
+    mdk::launch_set_rebuild(h->b, st);
+    mdk::launch_rebuild_chain(h->b, st);
+    return MD_OK;
+}
+
+md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, double *dL_dsigma, void *stream)
+{
+    if (!h || !dL_deuw || !dL_deps || !dL_dsigma) return fail(h, MD_ERR_ARG, "md_backward: null argument");
+    if (!h->ad_ready) return fail(h, MD_ERR_ARG, "md_backward without a recorded md_forward");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nrep = h->b.nrep;
+    const long long N = h->N, n3 = 3 * N;
+    const int T = h->ad_T, k = h->ad_k;
+    if (!h->ad_work && !(h->ad_work = dalloc<double>(h, (size_t)(4 * n3)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    if (h->ad_seg_cap < k + 1) {
+        h->ad_seg = grow(h, h->ad_seg, (size_t)((k + 1) * n3));
+        if (!h->ad_seg) return fail(h, MD_ERR_CUDA, "cannot allocate");
+        h->ad_seg_cap = k + 1;
+    }
+    if (!h->ad_small && !(h->ad_small = dalloc<double>(h, (size_t)(12 * nrep)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    double *lx = h->ad_work, *lv = lx + n3, *hv = lv + n3, *vzero = hv + n3;
+    double *coef = h->ad_small, *g = coef + 4 * nrep, *sums = g + 4 * nrep;
+    // loss weights (dL/dU, dL/dK, dL/dW) per replica, from host or device memory
+    std::vector<double> in(3 * nrep), cf(12 * nrep, 0.0);
+    if (!cuda_ok(h, cudaMemcpy(in.data(), dL_deuw, sizeof(double) * 3 * nrep, cudaMemcpyDefault), "read dL_deuw"))
+        return MD_ERR_CUDA;
+    for (int r = 0; r < nrep; ++r)
+        for (int q = 0; q < 3; ++q) cf[4 * r + q] = in[3 * r + q];
+    if (!cuda_ok(h, cudaMemcpyAsync(coef, cf.data(), sizeof(double) * 12 * nrep, cudaMemcpyHostToDevice, st), "upload") ||
+        !cuda_ok(h, cudaMemsetAsync(vzero, 0, sizeof(double) * n3, st), "clear"))
+        return MD_ERR_CUDA;
+    const double half = 0.5 * h->b.dt / h->b.mass;
+    // final state: adjoints of the loss and its explicit parameter terms
+    md_status s = adj_load(h, h->ad_fin, h->ad_fin + n3, st);
+    if (s != MD_OK) return s;
+    mdk::launch_adj_loss(h->b, coef, lx, lv, sums, st);
+    mdk::launch_adj_finish_loss(h->b, sums, coef, g, st);
+    // reverse through the steps, one checkpoint segment at a time (last first)
+    if (T > 0) {
+        const int nseg = (T + k - 1) / k;
+        for (int c = nseg - 1; c >= 0; --c) {
+            const int t0 = c * k, t1 = std::min(T, (c + 1) * k);
+            const double *ck = h->ad_ck + (long long)c * 2 * n3;
+            s = md_set_state(h, ck, ck + n3, st);
+            if (s != MD_OK) return s;
+            if (!cuda_ok(h, cudaMemcpyAsync(h->ad_seg, ck, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st), "copy"))
+                return MD_ERR_CUDA;
+            for (int t = t0 + 1; t <= t1; ++t) {
+                s = md_step(h, 1, 0, nullptr, stream);
+                if (s != MD_OK) return s;
+                mdk::launch_get_state(h->b, h->ad_seg + (long long)(t - t0) * n3, nullptr, st);
+            }
+            for (int t = t1; t >= (c == 0 ? 0 : t0 + 1); --t) {
+                s = adj_load(h, h->ad_seg + (long long)(t - t0) * n3, vzero, st);
+                if (s != MD_OK) return s;
+                // the kicks at x_t: the first half kick of step t and the second of step t - 1
+                const double ct = (t == T || t == 0) ? half : 2.0 * half;
+                mdk::launch_adj_hvp(h->b, lv, hv, ct, g, st);
+                mdk::launch_adj_update(n3, lx, lv, hv, ct, t > 0 ? h->b.dt : 0.0, st);
+            }
+        }
+    }
+    std::vector<double> gh(4 * nrep), ge(nrep), gs(nrep);
+    if (!cuda_ok(h, cudaMemcpyAsync(gh.data(), g, sizeof(double) * 4 * nrep, cudaMemcpyDeviceToHost, st), "read g"))
+        return MD_ERR_CUDA;
+    s = sync_and_check(h, st);
+    if (s != MD_OK) return s;
+    for (int r = 0; r < nrep; ++r) { ge[r] = gh[4 * r]; gs[r] = gh[4 * r + 1]; }
+    if (!cuda_ok(h, cudaMemcpy(dL_deps, ge.data(), sizeof(double) * nrep, cudaMemcpyDefault), "write dL_deps") ||
+        !cuda_ok(h, cudaMemcpy(dL_dsigma, gs.data(), sizeof(double) * nrep, cudaMemcpyDefault), "write dL_dsigma"))
+        return MD_ERR_CUDA;
+    // leave the handle at the final state of the recorded run
+    s = md_set_state(h, h->ad_fin, h->ad_fin + n3, st);
+    if (s != MD_OK) return s;
+    return sync_and_check(h, st);
 }
 
 md_status md_set_timing(md_handle *h, int32_t enable)

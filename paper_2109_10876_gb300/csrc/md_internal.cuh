@@ -264,5 +264,9 @@ void launch_kick_drift(const Bufs &b, cudaStream_t st);
 void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st);
 void launch_export_pairs(const Bufs &b, int *pairs, long long cap, unsigned long long *count, cudaStream_t st);
 void launch_set_rebuild(const Bufs &b, cudaStream_t st);
+void launch_adj_hvp(const Bufs &b, const double *w, double *hv, double scale, double *g, cudaStream_t st);
+void launch_adj_loss(const Bufs &b, const double *coef, double *lx, double *lv, double *sums, cudaStream_t st);
+void launch_adj_finish_loss(const Bufs &b, const double *sums, const double *coef, double *g, cudaStream_t st);
+void launch_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt, cudaStream_t st);
 
 }  // namespace mdk

@@ -101,6 +101,10 @@ _lib.md_sync.restype = C.c_int
 _lib.md_sync.argtypes = [_H, _vp]
 _lib.md_get_stats.restype = C.c_int
 _lib.md_get_stats.argtypes = [_H, C.POINTER(md_stats)]
+_lib.md_forward.restype = C.c_int
+_lib.md_forward.argtypes = [_H, C.c_int32, C.c_int32, _vp, _vp]
+_lib.md_backward.restype = C.c_int
+_lib.md_backward.argtypes = [_H, _vp, _vp, _vp, _vp]
 _lib.md_set_timing.restype = C.c_int
 _lib.md_set_timing.argtypes = [_H, C.c_int32]
 _lib.md_get_timing.restype = C.c_int
@@ -234,6 +238,14 @@ def md_compute_forces(h, f_out=None, euw_out=None, stream=None):
 
 def md_step(h, nsteps, thermo_every=0, thermo_out=None, stream=None):
     return _check(h.ptr, _lib.md_step(h.ptr, int(nsteps), int(thermo_every), _ptr(thermo_out), _stream(stream)))
+
+
+def md_forward(h, nsteps, ckpt_every, euw_out=None, stream=None):
+    return _check(h.ptr, _lib.md_forward(h.ptr, int(nsteps), int(ckpt_every), _ptr(euw_out), _stream(stream)))
+
+
+def md_backward(h, dL_deuw, dL_deps, dL_dsigma, stream=None):
+    return _check(h.ptr, _lib.md_backward(h.ptr, _ptr(dL_deuw), _ptr(dL_deps), _ptr(dL_dsigma), _stream(stream)))
 
 
 def md_export_pairs(h, pairs_out, capacity, stream=None):
