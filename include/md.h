@@ -94,6 +94,10 @@ typedef struct {
     int32_t ncell[3];           /* cell grid of replica 0                     */
     int32_t n_replicas;
     int64_t n_particles;
+    int32_t n_tiles;            /* tiles of the last build (runs of cells along x) */
+    int32_t max_halo;           /* largest tile halo (particles) at the last build */
+    int32_t halo_capacity;      /* shared-memory halo capacity (particles)    */
+    int32_t reserved1;
 } md_stats;
 
 /* Create a handle for the replicas described by p (Sec. 2.1: cells of edge

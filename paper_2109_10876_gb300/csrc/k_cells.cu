@@ -132,6 +132,14 @@ __global__ void k_get_state(Bufs b, double *xout, double *vout)
 
 __global__ void k_set_rebuild(Ctl *ctl) { ctl->rebuild = 1; }
 
+__global__ void k_cond(Ctl *ctl, cudaGraphConditionalHandle handle, int what)
+{
+    const unsigned v = what == 0 ? (ctl->rebuild != 0 && ctl->err == 0) : (ctl->steps_left > 0 && ctl->err == 0);
+    cudaGraphSetConditional(handle, v ? 1u : 0u);
+}
+
+__global__ void k_set_steps(Ctl *ctl, long long left) { ctl->steps_left = left; }
+
 // ---------------------------------------------------------------- counting sort
 // a1: cell id of every particle and the cell histogram.
 __global__ void k_bin(Bufs b)
@@ -754,6 +762,13 @@ void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st)
 }
 
 void launch_set_rebuild(const Bufs &b, cudaStream_t st) { k_set_rebuild<<<1, 1, 0, st>>>(b.ctl); }
+
+void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_t st)
+{
+    k_cond<<<1, 1, 0, st>>>(b.ctl, (cudaGraphConditionalHandle)handle, what);
+}
+
+void launch_set_steps(const Bufs &b, long long left, cudaStream_t st) { k_set_steps<<<1, 1, 0, st>>>(b.ctl, left); }
 
 static int list_grid(size_t smem)
 {

@@ -241,6 +241,11 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, flo
             b.ctl->rebuild = (__uint_as_float(bits) > 1.0f) ? 1 : 0;
             b.ctl->cur ^= 1;
             b.ctl->step += 1;
+            if (b.g_while) {                    // inside the graph's step loop
+                const long long left = b.ctl->steps_left - 1;
+                b.ctl->steps_left = left;
+                cudaGraphSetConditional(b.g_while, left > 0 ? 1u : 0u);
+            }
         }
         if (tiled) b.ctl->tile_next = 0u;
         b.ctl->done_force = 0u;

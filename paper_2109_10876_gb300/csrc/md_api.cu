@@ -50,6 +50,12 @@ struct md_handle {
     double *ad_seg = nullptr;       // positions of one segment: (k + 1) x 3 N
     long long ad_seg_cap = 0;
     double *ad_small = nullptr;     // coef (4 nrep), g (4 nrep), sums (4 nrep)
+    // the step loop as a CUDA graph (conditional WHILE over steps, IF over rebuilds)
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long gen = 0, gexec_gen = -1;   // bumped whenever the kernels' buffers change
+    bool use_graph = true;
 };
 
 namespace {
@@ -119,6 +125,7 @@ md_status alloc_list(md_handle *h, int K)
     }
     h->K = K;
     h->b.K = K;
+    h->gen++;
     h->b.nbr = dalloc<unsigned short>(h, (size_t)K * (size_t)h->S);
     if (!h->b.nbr) return fail(h, MD_ERR_CUDA, "cannot allocate the neighbour list");
     return MD_OK;
@@ -195,6 +202,96 @@ md_status sync_and_check(md_handle *h, cudaStream_t st)
     md_status s = read_ctl(h, &c);
     if (s != MD_OK) return s;
     return status_of(h, c.err);
+}
+
+// Capture f(stream) into graph g after deps; tail gets the captured sink nodes.
+template <class F>
+bool capture_into(md_handle *h, cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps, F f,
+                  std::vector<cudaGraphNode_t> *tail)
+{
+    if (cudaStreamBeginCaptureToGraph(h->cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return false;
+    f(h->cap);
+    if (tail) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *d = nullptr;
+        size_t nd = 0;
+        if (cudaStreamGetCaptureInfo(h->cap, &cs, nullptr, nullptr, &d, nullptr, &nd) != cudaSuccess) return false;
+        tail->assign(d, d + nd);
+    }
+    cudaGraph_t out = nullptr;
+    return cudaStreamEndCapture(h->cap, &out) == cudaSuccess;
+}
+
+// One graph for md_step(n > 0) without timers or energies:
+//   kick-drift -> cond(W: steps left) -> WHILE(W) { cond(I: rebuild) -> IF(I) { rebuild chain }
+//   -> fused force } -> cond(I2) -> IF(I2) { rebuild chain } -> final force.
+// The fused kernel's last block counts the steps down and sets W.
+bool build_step_graph(md_handle *h)
+{
+    if (h->gexec && h->gexec_gen == h->gen) return true;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+    cudaGraph_t G;
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
+    h->graph = G;
+    cudaGraphConditionalHandle hW, hI2;
+    if (cudaGraphConditionalHandleCreate(&hW, G, 0, 0) != cudaSuccess) return false;
+    if (cudaGraphConditionalHandleCreate(&hI2, G, 0, 0) != cudaSuccess) return false;
+    Bufs b = h->b;
+    b.g_while = 0;
+    const int prec = h->precision;
+    std::vector<cudaGraphNode_t> tail;
+    if (!capture_into(h, G, {}, [&](cudaStream_t s) {
+            mdk::launch_kick_drift(b, s);
+            mdk::launch_cond(b, hW, 1, s);
+        }, &tail))
+        return false;
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hW;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t nW;
+    if (cudaGraphAddNode(&nW, G, tail.data(), nullptr, tail.size(), &wp) != cudaSuccess) return false;
+    cudaGraph_t BW = wp.conditional.phGraph_out[0];
+    cudaGraphConditionalHandle hI;
+    if (cudaGraphConditionalHandleCreate(&hI, BW, 0, 0) != cudaSuccess) return false;
+    if (!capture_into(h, BW, {}, [&](cudaStream_t s) { mdk::launch_cond(b, hI, 0, s); }, &tail)) return false;
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hI;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t nI;
+    if (cudaGraphAddNode(&nI, BW, tail.data(), nullptr, tail.size(), &ip) != cudaSuccess) return false;
+    if (!capture_into(h, ip.conditional.phGraph_out[0], {}, [&](cudaStream_t s) { mdk::launch_rebuild_chain(b, s); },
+                      nullptr))
+        return false;
+    Bufs bf = b;
+    bf.g_while = hW;
+    if (!capture_into(h, BW, {nI}, [&](cudaStream_t s) { mdk::launch_force(bf, prec, mdk::kModeFused, false, s); },
+                      nullptr))
+        return false;
+    if (!capture_into(h, G, {nW}, [&](cudaStream_t s) { mdk::launch_cond(b, hI2, 0, s); }, &tail)) return false;
+    cudaGraphNodeParams ip2 = {};
+    ip2.type = cudaGraphNodeTypeConditional;
+    ip2.conditional.handle = hI2;
+    ip2.conditional.type = cudaGraphCondTypeIf;
+    ip2.conditional.size = 1;
+    cudaGraphNode_t nI2;
+    if (cudaGraphAddNode(&nI2, G, tail.data(), nullptr, tail.size(), &ip2) != cudaSuccess) return false;
+    if (!capture_into(h, ip2.conditional.phGraph_out[0], {}, [&](cudaStream_t s) { mdk::launch_rebuild_chain(b, s); },
+                      nullptr))
+        return false;
+    if (!capture_into(h, G, {nI2}, [&](cudaStream_t s) { mdk::launch_force(b, prec, mdk::kModeFinal, false, s); },
+                      nullptr))
+        return false;
+    if (cudaGraphInstantiate(&h->gexec, G, 0) != cudaSuccess) { h->gexec = nullptr; return false; }
+    h->gexec_gen = h->gen;
+    return true;
 }
 
 }  // namespace
@@ -444,6 +541,9 @@ void md_destroy(md_handle *h)
     cudaDeviceSynchronize();
     for (void *q : h->allocs) cudaFree(q);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
 
@@ -503,6 +603,7 @@ md_status md_build_neighbors(md_handle *h, void *stream)
             int hc = (int)round_up((long long)(c.max_halo * 1.25), 128);
             if (c.max_halo > lim) return fail(h, MD_ERR_LIST_OVERFLOW, "a cell neighbourhood exceeds the halo capacity");
             h->b.hcap = std::min(hc, lim);
+            h->gen++;
         }
         int zero = 0;
         if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
@@ -553,6 +654,17 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
     const long long nrec = thermo_every > 0 ? nsteps / thermo_every : 0;
     if (nrec > 0 && ensure_thermo(h, nrec * 3 * nrep) != MD_OK) return MD_ERR_CUDA;
     Bufs b = h->b;
+    if (!h->timing && nrec == 0 && h->use_graph && build_step_graph(h)) {
+        if (!h->F_valid) {
+            mdk::launch_rebuild_chain(b, st);
+            mdk::launch_force(b, h->precision, mdk::kModeStore, false, st);
+        }
+        mdk::launch_set_steps(b, (long long)nsteps - 1, st);
+        if (!cuda_ok(h, cudaGraphLaunch(h->gexec, st), "graph launch")) return MD_ERR_CUDA;
+        h->F_valid = true;
+        return MD_OK;
+    }
+    cudaGetLastError();   // a failed graph build leaves nothing behind: fall back to stream launches
     if (h->timing && h->ev_marks.size() > 100000) resolve_timing(h);   // bounded event pool
     long long t0 = mark(h, st);
     if (!h->F_valid) {
@@ -630,6 +742,9 @@ md_status md_get_stats(md_handle *h, md_stats *out)
     for (int k = 0; k < 3; ++k) out->ncell[k] = h->reps[0].ncell[k];
     out->n_replicas = h->b.nrep;
     out->n_particles = h->N;
+    out->n_tiles = c.ntiles;
+    out->max_halo = c.max_halo;
+    out->halo_capacity = h->b.hcap;
     return status_of(h, c.err);
 }
 

@@ -89,6 +89,7 @@ struct Ctl {
     unsigned tile_next;      // work counter of the persistent tile kernels
     int max_halo;            // largest halo of the current build
     long long step;          // index of the current positions x_step
+    long long steps_left;    // fused steps still to run in a graph-launched md_step
     long long rebuilds;
     long long list_entries;
 };
@@ -204,6 +205,7 @@ struct Bufs {
     double fene_K, fene_R02;
     float fene_K_f, fene_R02_f;
     unsigned long long seed;
+    unsigned long long g_while;  // graph conditional handle of the step loop (0 outside a graph)
 };
 
 // Asynchronous global -> shared copies (no register staging): every copy a
@@ -264,6 +266,9 @@ void launch_kick_drift(const Bufs &b, cudaStream_t st);
 void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st);
 void launch_export_pairs(const Bufs &b, int *pairs, long long cap, unsigned long long *count, cudaStream_t st);
 void launch_set_rebuild(const Bufs &b, cudaStream_t st);
+// graph conditionals: set `handle` to (ctl->rebuild != 0) (what = 0) or (ctl->steps_left > 0) (what = 1)
+void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_t st);
+void launch_set_steps(const Bufs &b, long long left, cudaStream_t st);
 void launch_adj_hvp(const Bufs &b, const double *w, double *hv, double scale, double *g, cudaStream_t st);
 void launch_adj_loss(const Bufs &b, const double *coef, double *lx, double *lv, double *sums, cudaStream_t st);
 void launch_adj_finish_loss(const Bufs &b, const double *sums, const double *coef, double *g, cudaStream_t st);

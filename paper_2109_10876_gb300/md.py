@@ -72,6 +72,10 @@ class md_stats(C.Structure):
         ("ncell", C.c_int32 * 3),
         ("n_replicas", C.c_int32),
         ("n_particles", C.c_int64),
+        ("n_tiles", C.c_int32),
+        ("max_halo", C.c_int32),
+        ("halo_capacity", C.c_int32),
+        ("reserved1", C.c_int32),
     ]
 
 
