@@ -184,6 +184,52 @@ def cpu_baseline(x, box, target_s=10.0):
                       f"(one particle-step each), {t:.1f} s"}
 
 
+def ensemble_leg(md, torch, dev, passes=3, nsteps=200, ckpt=20):
+    """Batched differentiable ensemble: 64 LJ-fluid replicas, N log-uniform in
+    [500, 32000], per-replica eps and sigma; one pass = set the initial state,
+    build the lists, nsteps forward steps with checkpoints every ckpt, and the
+    FP64 adjoint of the loss U/N + (2K + W)/(3V) per replica back to
+    d(loss)/d(eps, sigma).  All replicas share one handle and one launch per
+    kernel."""
+    from paper_2109_10876_gb300 import inputs
+    sizes, boxes, eps, sig, x, v = inputs.ensemble()
+    n = int(sizes.sum())
+    R = len(sizes)
+    h = md.md_create(sizes, boxes, eps=eps, sigma=sig, rc_over_sigma=RC, skin=SKIN, dt=DT,
+                     precision=md.MD_FP32_FIXED)
+    xt = torch.tensor(x.T.copy(), device=dev)
+    vt = torch.tensor(v.T.copy(), device=dev)
+    vol = np.prod(boxes, axis=1)
+    g = torch.tensor(np.stack([1.0 / sizes, 2.0 / (3.0 * vol), 1.0 / (3.0 * vol)], axis=1), device=dev)
+    euw = torch.zeros(R, 3, dtype=torch.float64, device=dev)
+    ge = torch.zeros(R, dtype=torch.float64, device=dev)
+    gs = torch.zeros(R, dtype=torch.float64, device=dev)
+
+    def one():
+        md.md_set_state(h, xt, vt)
+        md.md_build_neighbors(h)
+        md.md_forward(h, nsteps, ckpt, euw)
+        md.md_backward(h, g, ge, gs)
+
+    one()                                   # first use: allocations, untimed
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(passes):
+        one()
+    torch.cuda.synchronize()
+    dt_s = time.perf_counter() - t0
+    h.destroy()
+    return {"value": passes * n * nsteps / dt_s, "unit": "particle-steps/s (forward + adjoint)",
+            "ms_per_pass": 1e3 * dt_s / passes, "passes": passes, "replicas": R, "particles": n,
+            "n_min": int(sizes.min()), "n_max": int(sizes.max()), "steps": nsteps, "ckpt_every": ckpt,
+            "loss": "U/N + (2K + W)/(3V) per replica",
+            "dloss_deps_first3": [float(t) for t in ge[:3].cpu()],
+            "dloss_dsigma_first3": [float(t) for t in gs[:3].cpu()],
+            "workload": "64 LJ-fluid replicas (fcc sites with vacancies, rho sigma^3 = 0.8442), N log-uniform "
+                        "500-32000, eps in [0.9, 1.1], sigma in [0.95, 1.05], rc = 2.5 sigma, skin 0.3, dt 0.005; "
+                        "FP32 + fixed-point forward, FP64 adjoint, wall clock of whole passes"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -239,6 +285,7 @@ def main():
     h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
     md.md_set_state(h, xt, vt)
     md.md_build_neighbors(h)
+    tile_size = md.md_autotune(h, 10)     # tile size by timed trial steps (state restored)
     md.md_step(h, max(args.warmup, 3))
     md.md_sync(h)
     st0 = md.md_get_stats(h)
@@ -334,6 +381,8 @@ def main():
         extras["fp64"] = {"value": world * v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
                           "speedup_fp32_fixed_over_fp64": (value / world) / v64}
 
+        extras["ensemble"] = ensemble_leg(md, torch, dev)
+
         if world == 1 and rank == 0:
             import oracle
             # ---- force error of the FP32 path on a perturbed lattice of the same size
@@ -362,7 +411,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": f"LJ fluid N={n} per GPU (fcc {args.ncell}^3 x 4), rho={RHO}, T*={T0}, "
                                        f"rc={RC} shifted, skin={SKIN}, dt={DT}, NVE, FP32 pairs + 64-bit fixed-point "
-                                       f"sums", "particles_per_gpu": n,
+                                       f"sums", "particles_per_gpu": n, "tile_size": tile_size,
                            "parallelism": "replicas only" if world > 1 else "1 GPU",
                            "l2": "working set larger than L2 (positions, velocities and the Verlet list: "
                                  f"~{(n * (FORCE_FIXED_BYTES + list_bytes)) / 1e6:.0f} MB touched per step)"},

@@ -97,7 +97,7 @@ typedef struct {
     int32_t n_tiles;            /* tiles of the last build (runs of cells along x) */
     int32_t max_halo;           /* largest tile halo (particles) at the last build */
     int32_t halo_capacity;      /* shared-memory halo capacity (particles)    */
-    int32_t reserved1;
+    int32_t tile_size;          /* particles per tile the tiler aims at        */
 } md_stats;
 
 /* Create a handle for the replicas described by p (Sec. 2.1: cells of edge
@@ -166,6 +166,25 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
  * (2 * capacity int32) to pairs_out and the total count to *n_out (host).
  * Synchronises `stream`. */
 md_status md_export_pairs(md_handle *h, int32_t *pairs_out, int64_t capacity, int64_t *n_out, void *stream);
+
+/* Pick the tile size (particles per tile of the force and list kernels) by
+ * timing: starting from the largest (128), halve it while trial_steps steps
+ * get faster, down to 8.  This is the GPU counterpart of the paper's tuning of
+ * the HPX subnode count (Sec. 3.3, Sec. 4.2), which doubles the number of
+ * subnodes until the elapsed time of a few steps stops falling.  Positions,
+ * velocities, the stored force and the step counter are saved and restored,
+ * so the trajectory goes on from where it was (bit for bit in
+ * MD_FP32_FIXED, whose sums do not depend on the tiling); the rebuild
+ * statistics restart.  Takes 9N doubles of extra device memory for the
+ * duration of the call.  Writes the chosen size to *tile_max_out (host
+ * pointer, may be NULL).  Synchronous. */
+md_status md_autotune(md_handle *h, int32_t trial_steps, int32_t *tile_max_out, void *stream);
+
+/* Set the tile size by hand (1..128 particles; a tile always holds at least
+ * one whole cell, so cells fuller than the size make one-cell tiles).  The
+ * next step, force or list call re-sorts and rebuilds the list on `stream`.
+ * MD_ERR_ARG outside 1..128. */
+md_status md_set_tile_size(md_handle *h, int32_t tile_size, void *stream);
 
 /* Wait for all work on `stream` and return any latched device error. */
 md_status md_sync(md_handle *h, void *stream);

@@ -15,8 +15,7 @@ namespace mdk {
 __device__ __forceinline__ unsigned to_q(double y, double scale)
 {
     // y in [0, L): y * 2^32 / L in [0, 2^32]; 2^32 wraps to 0 (periodic).
-    long long q = __double2ll_rn(y * scale);
-    return (unsigned)(q & 0xffffffffLL);
+    return (unsigned)(fix_round(y, scale) & 0xffffffffLL);
 }
 
 __device__ __forceinline__ double wrap_box(double y, double L)
@@ -116,6 +115,22 @@ __global__ void k_set_state(Bufs b, const double *xin, const double *vin)
 }
 
 // Slot layout -> caller layout (3, N).
+// Stored force between slot order and caller (id) order: dir 0 copies out,
+// dir 1 copies in (after a re-sort, so that the stored force follows its
+// particles).
+__global__ void k_force_by_id(Bufs b, double *buf, int dir)
+{
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.S) return;
+    int id = (int)b.pos[b.ctl->cur][s].w;
+    if (id < 0) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (dir == 0) buf[k * b.N + id] = b.F[k * b.S + s];
+        else b.F[k * b.S + s] = buf[k * b.N + id];
+    }
+}
+
 __global__ void k_get_state(Bufs b, double *xout, double *vout)
 {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -335,7 +350,7 @@ __device__ int walk_row(const Bufs &b, int g, Tile *out, int *colsum, int *own)
             while (x1 < nx) {
                 const int c = mine(x1);
                 const int Hn = (x1 + 1 - x0 + 2 >= nx) ? total : H + col(wrapi(x1 + 1, nx));
-                if (P + c > kTileMax || Hn > b.hcap) break;
+                if (P + c > b.tile_max || Hn > b.hcap) break;
                 P += c;
                 H = Hn;
                 ++x1;
@@ -476,7 +491,7 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_tile_pieces(Bufs b)
 
 __host__ __device__ inline size_t list_smem_bytes(int hcap)
 {
-    return (size_t)hcap * sizeof(uint4) + (size_t)kListStage * kTileMax * sizeof(unsigned short);
+    return (size_t)hcap * sizeof(uint4) + (size_t)(kListStage * kTileMax + 32) * sizeof(unsigned short);
 }
 
 // Lists of the particles of one tile.  A warp takes 32 consecutive particles
@@ -488,9 +503,30 @@ __host__ __device__ inline size_t list_smem_bytes(int hcap)
 // r_skin) away and fails the distance test, so each list is exactly the pair
 // set, ordered by halo row and slot.  Distances in fixed-point units of the
 // x axis (see Replica).
+// One candidate batch of the list walk: squared separations of 4 halo
+// entries from this lane's particle in x-axis units.
+template <bool CUBIC>
+__device__ __forceinline__ float sep2(uint4 p, uint4 q, float ry, float rz)
+{
+    float d0 = (float)(int)(p.x - q.x);
+    float d1 = (float)(int)(p.y - q.y);
+    float d2 = (float)(int)(p.z - q.z);
+    if (!CUBIC) { d1 *= ry; d2 *= rz; }
+    return d0 * d0 + d1 * d1 + d2 * d2;
+}
+
+// Verlet lists of one tile (Sec. 2.1.2): each warp takes 32 consecutive
+// particles and walks the union of their 27-cell stencils, candidate by
+// candidate (a shared-memory broadcast), keeping j when |d_ij| < r_cut + r_skin.
+// Candidates whose FP32 r^2 lies within rounding of the list radius are
+// decided in FP64 from the master positions (one vote per batch of 4).
+// Appends are branch-free: every candidate is written at the lane's next free
+// row and the row pointer advances only on a hit.  The shared stage has the
+// final [row][particle] layout of the tile's list block; a list that outgrows
+// it is walked again straight into global memory (rare).
 template <bool CUBIC>
 __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
-                                              const uint4 *halo, unsigned short *lst, const double *X, const uint4 *P,
+                                              const uint4 *halo, unsigned short *lst, const double *X, int hfirst,
                                               int *s_kmax, int &mx, long long &sm, int &err)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -501,16 +537,9 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
     const int nrow = cntY * cntZ;
     const float lo = R.rl2_lo_u, hi = R.rl2_hi_u, ry = R.ry, rz = R.rz;
     const int Pt = tl.s1 - tl.s0;
-    const bool staged = Pt <= kTileMax;
-    const int crow = (-lz) * cntY + (-ly);          // halo row of the tile itself
-    // halo offset of the tile's first particle: its slots are contiguous in the
-    // piece(s) of the tile's own row
-    int hfirst = 0;
-    {
-        int q = 0;
-        while (q + 1 < np && !(pc[q].row == crow && pc[q].slot0 <= tl.s0 && tl.s0 < pc[q].slot0 + pc[q].n + (pc[q].n == 0))) ++q;
-        hfirst = pc[q].hoff + (tl.s0 - pc[q].slot0);
-    }
+    // stage rows of this tile (0: no stage, every list goes to global memory)
+    const int cap = Pt <= kTileMax ? min((kListStage * kTileMax) / max(Pt, 1), b.K) : 0;
+    unsigned short *dummy = lst + kListStage * kTileMax;     // one slot per lane
     for (int c0 = warp * 32; c0 < Pt; c0 += nwarp * 32) {
         const int pp = c0 + lane;
         const bool valid = pp < Pt;
@@ -545,14 +574,13 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 if (rh0 < pc[qq].hoff || rh1 > pc[qq].hoff + pc[qq].n) { err |= kErrList; rh1 = rh0; }
             }
         }
-        const int self = hfirst + pp;
-        const uint4 p = halo[valid ? self : hfirst + c0];
-        // Appends are branch-free: the candidate is always written at the
-        // lane's current count, which advances only on a hit, so a miss is
-        // overwritten by the next hit.  Lists that outgrow the shared stage
-        // are rebuilt below straight into global memory.
-        // (a tile wider than kTileMax has no stage: its lanes write a dummy column)
-        unsigned short *mylst = lst + (staged ? pp : 0);
+        const int self = valid ? hfirst + pp : -1;
+        const uint4 p = halo[hfirst + (valid ? pp : c0)];
+        // this lane's stage column (row stride Pt); lanes without one write a
+        // private dummy slot (stride 0)
+        const bool own = valid && cap > 0;
+        unsigned short *col = own ? lst + pp : dummy + lane;
+        const int stride = own ? Pt : 0;
         int cnt = 0;
         for (int r = 0; r < nrow * 2; ++r) {
             const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
@@ -562,58 +590,58 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 uint4 pj[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) pj[u] = halo[h + u];
+                float r2[4];
+                bool in[4];
+                bool bnd = false;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    float d0 = (float)(int)(p.x - pj[u].x);
-                    float d1 = (float)(int)(p.y - pj[u].y);
-                    float d2 = (float)(int)(p.z - pj[u].z);
-                    if (!CUBIC) { d1 *= ry; d2 *= rz; }
-                    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                    const bool mine = valid & (h + u != self);
-                    bool in = (r2 < lo) & mine;
-                    const bool band = (r2 < hi) & !(r2 < lo) & mine;
-                    if (__any_sync(0xffffffffu, band) && band)
-                        in = r2_fp64(X, b.S, i, j0 + (h + u - h0), R.L) < R.rl2;
-                    mylst[min(cnt, kListStage - 1) * kTileMax] = (unsigned short)(h + u);
-                    cnt += in;
+                    r2[u] = sep2<CUBIC>(p, pj[u], ry, rz);
+                    in[u] = (r2[u] < lo) & (h + u != self);
+                    bnd |= (r2[u] < hi) & !(r2[u] < lo);
+                }
+                if (__any_sync(0xffffffffu, bnd)) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (valid & (r2[u] < hi) & !(r2[u] < lo) & (h + u != self))
+                            in[u] = r2_fp64(X, b.S, i, j0 + (h + u - h0), R.L) < R.rl2;
+                }
+                // four free rows from here while cnt <= cap - 4 (else re-walked below)
+                unsigned short *q = col + max(min(cnt, cap - 4), 0) * stride;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    *q = (unsigned short)(h + u);
+                    q += in[u] ? stride : 0;
+                    cnt += in[u];
                 }
             }
             for (; h < h1; ++h) {
-                const uint4 pj = halo[h];
-                float d0 = (float)(int)(p.x - pj.x);
-                float d1 = (float)(int)(p.y - pj.y);
-                float d2 = (float)(int)(p.z - pj.z);
-                if (!CUBIC) { d1 *= ry; d2 *= rz; }
-                const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                const float r2 = sep2<CUBIC>(p, halo[h], ry, rz);
                 const bool mine = valid & (h != self);
                 bool in = (r2 < lo) & mine;
                 const bool band = (r2 < hi) & !(r2 < lo) & mine;
                 if (__any_sync(0xffffffffu, band) && band)
                     in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
-                mylst[min(cnt, kListStage - 1) * kTileMax] = (unsigned short)h;
+                col[max(min(cnt, cap - 4), 0) * stride] = (unsigned short)h;
                 cnt += in;
             }
         }
-        // a list longer than the stage (or a tile wider than kTileMax): walk
-        // the candidates again, writing to global memory (rare)
-        if (__any_sync(0xffffffffu, valid && (cnt >= kListStage || !staged))) {
+        // a list longer than the stage allows (or a tile without a stage):
+        // walk the candidates again; rows below cap go to the stage, the rest
+        // to global memory
+        const bool over = valid && (cnt > cap - 4);
+        if (__any_sync(0xffffffffu, over)) {
             int c2 = 0;
             for (int r = 0; r < nrow * 2; ++r) {
                 const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
                 const int j0 = __shfl_sync(0xffffffffu, rj0, r);
                 for (int h = h0; h < h1; ++h) {
-                    const uint4 pj = halo[h];
-                    float d0 = (float)(int)(p.x - pj.x);
-                    float d1 = (float)(int)(p.y - pj.y);
-                    float d2 = (float)(int)(p.z - pj.z);
-                    if (!CUBIC) { d1 *= ry; d2 *= rz; }
-                    const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                    const float r2 = sep2<CUBIC>(p, halo[h], ry, rz);
                     const bool mine = valid & (h != self);
                     bool in = (r2 < lo) & mine;
                     if ((r2 < hi) & !(r2 < lo) & mine) in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
-                    if (in && (cnt >= kListStage || !staged)) {
-                        if (c2 < b.K) b.nbr[nbr_index(tl.s0, Pt, b.K, c2, pp)] = (unsigned short)h;
-                        if (staged && c2 < kListStage) lst[c2 * kTileMax + pp] = (unsigned short)h;
+                    if (in && over) {
+                        if (c2 < cap) lst[c2 * Pt + pp] = (unsigned short)h;
+                        else if (c2 < b.K) b.nbr[nbr_index(tl.s0, Pt, b.K, c2, pp)] = (unsigned short)h;
                     }
                     c2 += in;
                 }
@@ -623,8 +651,8 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             // pad with the particle's own index (r = 0 is never an interaction)
             const int kp = min(((cnt + kPad - 1) / kPad) * kPad, b.K);
             for (int k = cnt; k < kp; ++k) {
-                if (staged && k < kListStage) lst[k * kTileMax + pp] = (unsigned short)self;
-                if (!staged || k >= kListStage) b.nbr[nbr_index(tl.s0, Pt, b.K, k, pp)] = (unsigned short)self;
+                if (k < cap) lst[k * Pt + pp] = (unsigned short)self;
+                else b.nbr[nbr_index(tl.s0, Pt, b.K, k, pp)] = (unsigned short)self;
             }
             b.nn[i] = cnt;
             if (cnt > b.K) err |= kErrList;
@@ -639,7 +667,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
     extern __shared__ uint4 halo[];
-    unsigned short *lst = reinterpret_cast<unsigned short *>(halo + b.hcap);   // [k][p], p < kTileMax
+    unsigned short *lst = reinterpret_cast<unsigned short *>(halo + b.hcap);   // [k][Pt] stage, then 32 dummy slots
     __shared__ Piece pc[kMaxPieces + 1];
     __shared__ Tile tl;
     __shared__ int s_tile, s_np, s_kmax;
@@ -674,17 +702,20 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
         stage_halo<uint4>(pc, s_np, [&](int h, int j) { cp_async16(&halo[h], &P[j]); });
         cp_async_wait_all();
         __syncthreads();
-        if (R.cubic) cells_of_tile<true>(b, R, tl, pc, s_np, halo, lst, X, P, &s_kmax, mx, sm, err);
-        else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, P, &s_kmax, mx, sm, err);
+        const int hfirst = tile_self_offset(R, tl, pc, s_np);
+        if (R.cubic) cells_of_tile<true>(b, R, tl, pc, s_np, halo, lst, X, hfirst, &s_kmax, mx, sm, err);
+        else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, &s_kmax, mx, sm, err);
         __syncthreads();
         if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;
-        // staged rows out to global memory, contiguous per row
-        const int kr = (Pt <= kTileMax) ? min(s_kmax, kListStage) : 0, pr = Pt;
+        // the staged rows are the start of the tile's list block: one
+        // contiguous copy (the block starts 64-byte aligned)
+        const int cap = Pt <= kTileMax ? min((kListStage * kTileMax) / max(Pt, 1), b.K) : 0;
+        const int total = min(s_kmax, cap) * Pt;
         unsigned short *dst = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
-        for (int idx = threadIdx.x; idx < kr * pr; idx += blockDim.x) {
-            const int k = idx / pr, pq = idx - k * pr;
-            dst[(long long)k * Pt + pq] = lst[k * kTileMax + pq];
-        }
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(lst);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (int m = threadIdx.x; m < (total >> 3); m += blockDim.x) d4[m] = s4[m];
+        for (int m = ((total >> 3) << 3) + threadIdx.x; m < total; m += blockDim.x) dst[m] = lst[m];
         if (threadIdx.x == 0) s_tile = t_next;
         __syncthreads();
     }
@@ -768,6 +799,10 @@ void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_
     k_cond<<<1, 1, 0, st>>>(b.ctl, (cudaGraphConditionalHandle)handle, what);
 }
 
+void launch_force_by_id(const Bufs &b, double *buf, int dir, cudaStream_t st)
+{
+    k_force_by_id<<<(unsigned)((b.S + 255) / 256), 256, 0, st>>>(b, buf, dir);
+}
 void launch_set_steps(const Bufs &b, long long left, cudaStream_t st) { k_set_steps<<<1, 1, 0, st>>>(b.ctl, left); }
 
 static int list_grid(size_t smem)

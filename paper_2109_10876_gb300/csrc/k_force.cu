@@ -64,13 +64,7 @@ __device__ __forceinline__ void fx_acc(float f, unsigned &hi, unsigned &lo)
 __device__ __forceinline__ double fx_value(unsigned hi, unsigned lo)
 {
     long long v = (long long)(int)hi * 4194304LL + (long long)(int)lo;
-    return (double)v * kFixInv;
-}
-
-__device__ __forceinline__ unsigned to_q2(double y, double scale)
-{
-    long long q = __double2ll_rn(y * scale);
-    return (unsigned)(q & 0xffffffffLL);
+    return ll_to_double(v) * kFixInv;
 }
 
 __device__ __forceinline__ double wrap1(double y, double L)
@@ -188,10 +182,10 @@ __device__ __forceinline__ float drift(const Bufs &b, const Replica &R, long lon
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         double y = xi[k] + b.dt * v[k];
-        long long qq = __double2ll_rn(y * R.to_q[k]);
+        long long qq = fix_round(y, R.to_q[k]);
         if ((unsigned long long)qq >= 4294967296ULL) {
             y = wrap1(y, R.L[k]);
-            qq = __double2ll_rn(y * R.to_q[k]);
+            qq = fix_round(y, R.to_q[k]);
         }
         b.x[nxt][k * b.S + i] = y;
         b.v[nxt][k * b.S + i] = v[k];
@@ -348,7 +342,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Piece pc[kMaxPieces + 1];
     __shared__ Tile tl;
-    __shared__ int s_tile, s_np;
+    __shared__ int s_tile, s_np, s_self;
+    __shared__ int s_nn[kTileMax];
     __shared__ double sm3[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
     if (b.ctl->err) return;
@@ -382,6 +377,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             __syncthreads();
             continue;
         }
+        const bool own_staged = Pt <= kTileMax;
+        if (own_staged)
+            for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
+        if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
         if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
         else stage_halo<double>(pc, np, [&](int h, int j) {
             cp_async8(&hx[h], &X[j]);
@@ -389,7 +388,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             cp_async8(&hz[h], &X[2 * b.S + j]);
         });
         // the tile's lists: kmax rows of Pt entries, one contiguous block
-        const bool lstaged = tl.kmax <= kListStage && Pt <= kTileMax;
+        const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
         if (lstaged) {
             const unsigned short *src = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
             const int total = tl.kmax * Pt;            // entries; the block starts 64-byte aligned
@@ -403,8 +402,14 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         __syncthreads();
         double ui = 0.0, wi = 0.0, ki = 0.0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
-            const uint4 pi = P[i];
-            const int n = min(b.nn[i], b.K);
+            if (MODE == kModeFused) {
+                // this particle's integration state, needed after the pair loop
+                prefetch_l1(&b.v[cur][i]); prefetch_l1(&b.v[cur][b.S + i]); prefetch_l1(&b.v[cur][2 * b.S + i]);
+                prefetch_l1(&X[i]); prefetch_l1(&X[b.S + i]); prefetch_l1(&X[2 * b.S + i]);
+                prefetch_l1(&b.xref[i]);
+            }
+            const uint4 pi = (PREC == 1) ? hpos[s_self + (int)(i - tl.s0)] : P[i];
+            const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
             const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));   // entry k at nb[k Pt]
             double Fd[3] = {0.0, 0.0, 0.0};
@@ -422,7 +427,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 const unsigned hs[3] = {a.hx, a.hy, a.hz}, ls[3] = {a.lx, a.ly, a.lz};
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    Fd[k] = (double)((long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k]);
+                    Fd[k] = ll_to_double((long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k]);
                 fscale = kFixInv;
                 if (ENERGY) { ui += 0.5 * fx_value(a.hu, a.lu); wi += 0.5 * fx_value(a.hw, a.lw); }
             } else {
@@ -476,9 +481,9 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                         if (!(qf > 0.0f)) { err |= kErrBond; continue; }
                         const float c = -b.fene_K_f / qf;
                         unsigned h = 0, l = 0;
-                        fx_acc2(c, dx, h, l); Fd[0] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
-                        fx_acc2(c, dy, h, l); Fd[1] += (double)((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
-                        fx_acc2(c, dz, h, l); Fd[2] += (double)((long long)(int)h * 4194304LL + (long long)(int)l);
+                        fx_acc2(c, dx, h, l); Fd[0] += ll_to_double((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
+                        fx_acc2(c, dy, h, l); Fd[1] += ll_to_double((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
+                        fx_acc2(c, dz, h, l); Fd[2] += ll_to_double((long long)(int)h * 4194304LL + (long long)(int)l);
                         if (ENERGY) {
                             ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log((double)qf));
                             wi += 0.5 * (double)(c * r2);

@@ -446,6 +446,7 @@ md_status md_create(const md_params *p, md_handle **out)
     b.C = h->C;
     b.nrows = h->nrows;
     b.hcap = hcap;
+    b.tile_max = mdk::kTileMax;
     b.nrep = nrep;
     b.nblk = h->nblk;
     b.dt = p->dt;
@@ -745,6 +746,7 @@ md_status md_get_stats(md_handle *h, md_stats *out)
     out->n_tiles = c.ntiles;
     out->max_halo = c.max_halo;
     out->halo_capacity = h->b.hcap;
+    out->tile_size = h->b.tile_max;
     return status_of(h, c.err);
 }
 
@@ -866,6 +868,79 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
     s = md_set_state(h, h->ad_fin, h->ad_fin + n3, st);
     if (s != MD_OK) return s;
     return sync_and_check(h, st);
+}
+
+md_status md_set_tile_size(md_handle *h, int32_t tile_size, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    if (tile_size < 1 || tile_size > mdk::kTileMax) return fail(h, MD_ERR_ARG, "md_set_tile_size: size outside 1..128");
+    if (tile_size == h->b.tile_max) return MD_OK;
+    h->b.tile_max = tile_size;
+    h->gen++;   // the step graph holds the old Bufs by value
+    if (h->state_set) {
+        mdk::launch_set_rebuild(h->b, (cudaStream_t)stream);
+        if (!cuda_ok(h, cudaGetLastError(), "set_rebuild launch")) return MD_ERR_CUDA;
+    }
+    return MD_OK;
+}
+
+md_status md_autotune(md_handle *h, int32_t trial_steps, int32_t *tile_max_out, void *stream)
+{
+    if (!h || trial_steps < 1) return fail(h, MD_ERR_ARG, "md_autotune: bad arguments");
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_autotune before md_set_state");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n3 = 3 * h->N;
+    // saved: x, v and the stored force in caller order, and the step counter
+    double *save = dalloc<double>(h, (size_t)(3 * n3));
+    if (!save) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    const bool had_F = h->F_valid;
+    mdk::launch_get_state(h->b, save, save + n3, st);
+    if (had_F) mdk::launch_force_by_id(h->b, save + 2 * n3, 0, st);
+    if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
+    Ctl c0;
+    if (read_ctl(h, &c0) != MD_OK) return MD_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 0.f;
+    int best = h->b.tile_max;
+    md_status s = MD_OK;
+    // the sweep of the paper's subnode count: halve the task size while it helps
+    for (int cap = mdk::kTileMax; cap >= 8; cap /= 2) {
+        if ((s = md_set_tile_size(h, cap, stream)) != MD_OK) break;
+        if ((s = md_set_state(h, save, save + n3, st)) != MD_OK) break;
+        if ((s = md_build_neighbors(h, stream)) != MD_OK) break;
+        if ((s = md_step(h, 2, 0, nullptr, stream)) != MD_OK) break;
+        cudaEventRecord(e0, st);
+        if ((s = md_step(h, trial_steps, 0, nullptr, stream)) != MD_OK) break;
+        cudaEventRecord(e1, st);
+        if ((s = sync_and_check(h, st)) != MD_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (cap == mdk::kTileMax || ms < best_ms) { best_ms = ms; best = cap; }
+        else break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == MD_OK) s = md_set_tile_size(h, best, stream);
+    if (s == MD_OK) s = md_set_state(h, save, save + n3, st);
+    // the step counter (and with it the Langevin noise stream) carries on
+    if (s == MD_OK && !cuda_ok(h, cudaMemcpyAsync(&h->b.ctl->step, &c0.step, sizeof(long long),
+                                                  cudaMemcpyHostToDevice, st), "restore step"))
+        s = MD_ERR_CUDA;
+    if (s == MD_OK) s = md_build_neighbors(h, stream);
+    // the stored force (with its Langevin terms) follows the re-sorted particles
+    if (s == MD_OK && had_F) {
+        mdk::launch_force_by_id(h->b, save + 2 * n3, 1, st);
+        if (cuda_ok(h, cudaGetLastError(), "force restore")) h->F_valid = true;
+        else s = MD_ERR_CUDA;
+    }
+    if (s == MD_OK) s = sync_and_check(h, st);
+    cudaStreamSynchronize(st);
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+        if (*it == save) { cudaFree(*it); h->allocs.erase(it); break; }
+    if (tile_max_out) *tile_max_out = best;
+    return s;
 }
 
 md_status md_set_timing(md_handle *h, int32_t enable)

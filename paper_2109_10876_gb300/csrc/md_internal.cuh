@@ -101,7 +101,7 @@ struct Tile {
     int kmax;   // longest padded list of the tile (written by the list build)
 };
 
-constexpr int kListStage = 88;       // list rows of a tile staged in shared memory
+constexpr int kListStage = 104;      // list rows of a full tile staged in shared memory (x kTileMax entries)
 
 // One contiguous slot range of a halo: cells [xa, xb) of halo row `row`,
 // placed at halo offset hoff.
@@ -188,6 +188,7 @@ struct Bufs {
     int *rep_tile;           // nrep + 1: first tile of every replica
     int nrows;               // rows over all replicas
     int hcap;                // halo capacity (particles) of the tile kernels
+    int tile_max;            // particles per tile the tiler aims at (<= kTileMax; autotuned)
     const Replica *rep;      // n_rep
     const int *blk_rep;      // replica of every block of kBlock slots
     const int *bond_off;     // N + 1, bonds of particle id (both directions)
@@ -223,6 +224,17 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_l1(const void *gmem)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(gmem));
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -236,6 +248,41 @@ __device__ __forceinline__ void load_tile(const Bufs &b, int t, Tile &tl, Piece 
     int *dst = reinterpret_cast<int *>(pc);
     constexpr int words = (kMaxPieces + 1) * sizeof(Piece) / sizeof(int);
     for (int m = threadIdx.x; m < words; m += blockDim.x) dst[m] = src[m];
+}
+
+// Halo index of the tile's first particle.  The tile's own cells lie,
+// contiguous, inside one piece of its own row (pieces split only at the
+// periodic boundary, which a tile does not straddle).
+__device__ __forceinline__ int tile_self_offset(const Replica &R, const Tile &tl, const Piece *pc, int np)
+{
+    int ly, cntY, lz, cntZ;
+    axis_offsets(R.ncell[1], ly, cntY);
+    axis_offsets(R.ncell[2], lz, cntZ);
+    const int crow = (-lz) * cntY + (-ly);
+    int q = 0;
+    while (q + 1 < np && !(pc[q].row == crow && pc[q].slot0 <= tl.s0 &&
+                           tl.s0 < pc[q].slot0 + pc[q].n + (pc[q].n == 0)))
+        ++q;
+    return pc[q].hoff + (tl.s0 - pc[q].slot0);
+}
+
+// Exact conversions between FP64 and 64-bit integers by adding and removing
+// 1.5 * 2^52, whose unit in the last place is 1 (valid for |value| < 2^51).
+// They replace the integer <-> FP64 conversion instructions, which are slow
+// on this part's narrow FP64 pipe.
+constexpr double kRound52 = 6755399441055744.0;          // 1.5 * 2^52
+constexpr long long kRound52Bits = 0x4338000000000000LL;
+
+// round(y * scale) to nearest (ties to even), one rounding of the exact product
+__device__ __forceinline__ long long fix_round(double y, double scale)
+{
+    return __double_as_longlong(__fma_rn(y, scale, kRound52)) - kRound52Bits;
+}
+
+// the double equal to v (exact)
+__device__ __forceinline__ double ll_to_double(long long v)
+{
+    return __dsub_rn(__longlong_as_double(v + kRound52Bits), kRound52);
 }
 
 // Flat copy of a tile's halo (all loads independent): element h of piece q.
@@ -264,6 +311,7 @@ void launch_rebuild_chain(const Bufs &b, cudaStream_t st);
 void launch_force(const Bufs &b, int precision, int mode, bool energy, cudaStream_t st);
 void launch_kick_drift(const Bufs &b, cudaStream_t st);
 void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st);
+void launch_force_by_id(const Bufs &b, double *buf, int dir, cudaStream_t st);
 void launch_export_pairs(const Bufs &b, int *pairs, long long cap, unsigned long long *count, cudaStream_t st);
 void launch_set_rebuild(const Bufs &b, cudaStream_t st);
 // graph conditionals: set `handle` to (ctl->rebuild != 0) (what = 0) or (ctl->steps_left > 0) (what = 1)

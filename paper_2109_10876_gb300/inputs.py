@@ -237,3 +237,46 @@ def chains(nchain, nbead, box, seed, bond=0.97, rmin=0.75):
                 bonds.append((len(pts) - 1, len(pts)))
             pts.append(p)
     return wrap(np.array(pts), box), np.array(bonds, dtype=np.int32)
+
+
+def lattice_fluid(n, rho=0.8442, T=0.72, seed=1, sigma=1.0, amp=0.05):
+    """n particles at number density rho (in units of sigma^-3) in a cubic box
+    of edge L = sigma (n / rho)^(1/3): the sites of the smallest fcc lattice
+    with at least n sites, scaled to the box, with 4 k^3 - n of them chosen at
+    random and left empty, then uniform displacements in [-amp, amp] sigma;
+    Gaussian velocities at T.  Returns (x, v, box)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = sigma * (n / rho) ** (1.0 / 3.0)
+    k = 1
+    while 4 * k ** 3 < n:
+        k += 1
+    a = L / k
+    g = np.arange(k, dtype=np.float64)
+    cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
+    cells = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    sites = (cells[:, None, :] + FCC_BASIS[None, :, :]).reshape(-1, 3) * a
+    keep = np.sort(rng.permutation(len(sites))[:n])
+    box = np.array([L, L, L])
+    x = wrap(sites[keep] + rng.uniform(-amp * sigma, amp * sigma, size=(n, 3)), box)
+    v = maxwell_velocities(n, T, seed + 7919)
+    return x, v, box
+
+
+def ensemble(nrep=64, nmin=500, nmax=32000, rho=0.8442, T=0.72, seed=11,
+             eps_range=(0.9, 1.1), sigma_range=(0.95, 1.05)):
+    """Batched ensemble of LJ-fluid replicas: sizes log-uniform in [nmin, nmax],
+    per-replica eps and sigma uniform in the given ranges, each replica a
+    lattice_fluid at density rho in units of its own sigma.  Returns
+    (sizes (R,), boxes (R, 3), eps (R,), sigma (R,), x (N, 3), v (N, 3)) with
+    the replicas concatenated in order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), size=nrep))).astype(np.int64)
+    eps = rng.uniform(eps_range[0], eps_range[1], size=nrep)
+    sig = rng.uniform(sigma_range[0], sigma_range[1], size=nrep)
+    xs, vs, boxes = [], [], []
+    for r in range(nrep):
+        x, v, box = lattice_fluid(int(sizes[r]), rho, T, seed + 101 * (r + 1), sigma=float(sig[r]))
+        xs.append(x)
+        vs.append(v)
+        boxes.append(box)
+    return sizes, np.array(boxes), eps, sig, np.concatenate(xs), np.concatenate(vs)

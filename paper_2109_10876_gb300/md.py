@@ -75,7 +75,7 @@ class md_stats(C.Structure):
         ("n_tiles", C.c_int32),
         ("max_halo", C.c_int32),
         ("halo_capacity", C.c_int32),
-        ("reserved1", C.c_int32),
+        ("tile_size", C.c_int32),
     ]
 
 
@@ -109,6 +109,10 @@ _lib.md_forward.restype = C.c_int
 _lib.md_forward.argtypes = [_H, C.c_int32, C.c_int32, _vp, _vp]
 _lib.md_backward.restype = C.c_int
 _lib.md_backward.argtypes = [_H, _vp, _vp, _vp, _vp]
+_lib.md_autotune.restype = C.c_int
+_lib.md_autotune.argtypes = [_H, C.c_int32, C.POINTER(C.c_int32), _vp]
+_lib.md_set_tile_size.restype = C.c_int
+_lib.md_set_tile_size.argtypes = [_H, C.c_int32, _vp]
 _lib.md_set_timing.restype = C.c_int
 _lib.md_set_timing.argtypes = [_H, C.c_int32]
 _lib.md_get_timing.restype = C.c_int
@@ -256,6 +260,17 @@ def md_export_pairs(h, pairs_out, capacity, stream=None):
     n = C.c_int64(0)
     _check(h.ptr, _lib.md_export_pairs(h.ptr, _ptr(pairs_out), int(capacity), C.byref(n), _stream(stream)))
     return n.value
+
+
+def md_autotune(h, trial_steps=20, stream=None):
+    """md_autotune: returns the chosen tile size (particles per tile)."""
+    out = C.c_int32(0)
+    _check(h.ptr, _lib.md_autotune(h.ptr, int(trial_steps), C.byref(out), _stream(stream)))
+    return out.value
+
+
+def md_set_tile_size(h, tile_size, stream=None):
+    return _check(h.ptr, _lib.md_set_tile_size(h.ptr, int(tile_size), _stream(stream)))
 
 
 def md_sync(h, stream=None):
