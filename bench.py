@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ncell", type=int, default=NCELL)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64, CPU baseline and force error")
+    ap.add_argument("--workload", default="lj", choices=["lj", "melt", "slab"],
+                    help="lj: the LJ fluid line (default); melt / slab: one line for that workload")
     return ap.parse_args()
 
 
@@ -230,6 +232,102 @@ def ensemble_leg(md, torch, dev, passes=3, nsteps=200, ckpt=20):
                         "FP32 + fixed-point forward, FP64 adjoint, wall clock of whole passes"}
 
 
+def timed_steps(md, torch, h, steps, stream):
+    """Graph-launched md_step(steps) between CUDA events, with clocks sampled."""
+    clocks = Clocks(torch.cuda.current_device())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st0 = md.md_get_stats(h)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    md.md_step(h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    st1 = md.md_get_stats(h)
+    return e0.elapsed_time(e1), st0, st1, ck
+
+
+def workload_line(md, torch, dev, args, name, n, h, prep, extra):
+    stream = torch.cuda.current_stream()
+    md.md_step(h, max(args.warmup, 3))
+    md.md_sync(h)
+    ms, st0, st1, ck = timed_steps(md, torch, h, args.steps, stream)
+    rb = st1["rebuilds"] - st0["rebuilds"]
+    line = {"metric": f"{name} particle-steps/s", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+fixed64 (f64 integration)", "data": "synthetic",
+            "config": dict(extra, particles=n, tile_size=st1["tile_size"]),
+            "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + 9 * rb,
+            "mean_list_len": st1["list_entries"] / n, "max_list_len": st1["max_list_len"],
+            "max_cell_occupancy": st1["max_cell_occupancy"], "tiles": st1["n_tiles"],
+            "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck}
+    print(json.dumps(line), flush=True)
+
+
+def run_melt(md, torch, dev, args):
+    """Polymer melt: 2000 linear chains of 200 beads at bead density 0.85,
+    WCA (r_cut = 2^(1/6)) on all pairs, FENE K = 30, R0 = 1.5, Langevin
+    gamma = 0.5 at T = 1, dt = 0.01, skin 0.4.  Preparation (untimed): free
+    random walks (bond 0.97), the cosine push-off with A ramped 1 -> 100
+    (FP64, dt 0.005), then 300 WCA steps at dt 0.005."""
+    from paper_2109_10876_gb300 import inputs
+    t0 = time.perf_counter()
+    x, v, box, bonds = inputs.melt(2000, 200, rho=0.85, T=1.0, seed=4)
+    n = len(x)
+    xt = torch.tensor(x.T.copy(), device=dev)
+    vt = torch.tensor(v.T.copy(), device=dev)
+    rc = 2 ** (1 / 6)
+    common = dict(skin=0.4, bonds=bonds, fene_K=30.0, fene_R0=1.5, langevin_gamma=0.5, kT=1.0)
+    for k, A in enumerate((1.0, 2.0, 5.0, 10.0, 20.0, 50.0, 100.0)):
+        hp = md.md_create(n, box, potential=md.MD_SOFT, rc_over_sigma=rc, eps=A, dt=0.005,
+                          precision=md.MD_FP64, seed=100 + k, **common)
+        md.md_set_state(hp, xt, vt)
+        md.md_build_neighbors(hp)
+        md.md_step(hp, 300)
+        md.md_get_state(hp, xt, vt)
+        hp.destroy()
+    hw = md.md_create(n, box, potential=md.MD_WCA, dt=0.005, precision=md.MD_FP32_FIXED, seed=200, **common)
+    md.md_set_state(hw, xt, vt)
+    md.md_build_neighbors(hw)
+    md.md_step(hw, 300)
+    md.md_get_state(hw, xt, vt)
+    hw.destroy()
+    h = md.md_create(n, box, potential=md.MD_WCA, dt=0.01, precision=md.MD_FP32_FIXED, seed=4, **common)
+    md.md_set_state(h, xt, vt)
+    md.md_build_neighbors(h)
+    md.md_autotune(h, 10)
+    prep = f"free random walks, cosine push-off A = 1..100 (7 x 300 FP64 steps), 300 WCA steps at dt 0.005: " \
+           f"{time.perf_counter() - t0:.1f} s"
+    workload_line(md, torch, dev, args, "polymer melt", n, h, prep,
+                  {"workload": f"Kremer-Grest melt, 2000 x 200 linear chains (N = {n}), bead density 0.85, "
+                               f"WCA + FENE (K 30, R0 1.5) + Langevin (gamma 0.5, T 1), dt 0.01, skin 0.4",
+                   "l2": "working set about 60 MB (below L2); the timed steps run back to back"})
+    h.destroy()
+
+
+def run_slab(md, torch, dev, args):
+    """Liquid/vapour slab: 1,000,000 LJ particles, Lz = 4 Lx = 4 Ly, liquid at
+    0.80 in the central quarter of z, vapour at 0.02 elsewhere, random
+    sequential placement with minimum separation 0.8, T = 0.8, rc 2.5,
+    skin 0.3, dt 0.005, NVE."""
+    from paper_2109_10876_gb300 import inputs
+    t0 = time.perf_counter()
+    x, v, box = inputs.slab(1_000_000, rho_l=0.80, rho_v=0.02, T=0.8, seed=3, rmin=0.8)
+    n = len(x)
+    h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+    md.md_set_state(h, torch.tensor(x.T.copy(), device=dev), torch.tensor(v.T.copy(), device=dev))
+    md.md_build_neighbors(h)
+    md.md_autotune(h, 10)
+    prep = f"random sequential placement of 1e6 particles: {time.perf_counter() - t0:.1f} s"
+    workload_line(md, torch, dev, args, "liquid/vapour slab", n, h, prep,
+                  {"workload": f"LJ liquid/vapour slab, N = {n}, box {box[0]:.3f} x {box[1]:.3f} x {box[2]:.3f}, "
+                               f"liquid 0.80 / vapour 0.02, T* 0.8, rc 2.5, skin 0.3, dt 0.005, NVE",
+                   "l2": "working set about 160 MB (larger than L2)"})
+    h.destroy()
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -276,6 +374,12 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
+    if args.workload == "melt":
+        run_melt(md, torch, dev, args)
+        return
+    if args.workload == "slab":
+        run_slab(md, torch, dev, args)
+        return
     x, v, box = inputs.lj_fluid(args.ncell, rho=RHO, T=T0, seed=2 + rank)
     n = len(x)
     xt = torch.tensor(x.T.copy(), device=dev)

@@ -52,7 +52,12 @@ typedef enum {
     MD_ERR_BOX_TOO_SMALL = -8   /* a box edge is shorter than 2 (r_cut + r_skin) */
 } md_status;
 
-enum { MD_LJ = 0, MD_WCA = 1 };            /* md_params.potential */
+/* md_params.potential.  MD_SOFT is the cosine push-off A (1 + cos(pi r / r_cut))
+ * for r < r_cut, A = eps, r_cut = rc_over_sigma * sigma: a bounded repulsion
+ * that separates overlapping beads when a polymer melt is prepared (the melt
+ * of Sec. 4; the paper does not state its preparation).  MD_FP64 only, and
+ * not covered by md_forward / md_backward. */
+enum { MD_LJ = 0, MD_WCA = 1, MD_SOFT = 2 };
 enum { MD_FP64 = 0, MD_FP32_FIXED = 1 };   /* md_params.precision */
 
 /* Parameters of a set of independent replicas (n_replicas >= 1).  Replica r
@@ -66,11 +71,13 @@ typedef struct {
     const double *eps;              /* per replica, Eq. 2 epsilon               */
     const double *sigma;            /* per replica, Eq. 2 sigma                 */
     double rc_over_sigma;           /* cutoff in units of sigma (LJ fluid: 2.5);
-                                       ignored for MD_WCA (2^(1/6))             */
+                                       ignored for MD_WCA (2^(1/6)); MD_SOFT:
+                                       its r_cut / sigma                        */
     double skin;                    /* Verlet skin r_skin (absolute)            */
     double dt;                      /* time step                                */
     double mass;                    /* particle mass                            */
-    int32_t potential;              /* MD_LJ (shifted to 0 at r_cut) or MD_WCA  */
+    int32_t potential;              /* MD_LJ (shifted to 0 at r_cut), MD_WCA or
+                                       MD_SOFT                                  */
     int32_t precision;              /* MD_FP32_FIXED or MD_FP64                 */
     double langevin_gamma;          /* 0 = NVE                                  */
     double kT;                      /* Langevin temperature                     */

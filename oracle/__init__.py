@@ -6,6 +6,8 @@ velocities and forces are (N, 3) float64 arrays here.
 
 What each function follows in arXiv:2109.10876:
   lj_energy / lj_force      Eq. 2 (LJ pair potential), F = -dV/dr (Eq. 1)
+  soft_energy / soft_force  cosine push-off for overlapping chains (the melt of
+                            Sec. 4 needs a preparation the paper leaves open)
   forces                    direct O(N^2) minimum-image pair sum under r < r_cut
   forces_sample             the same sum for chosen particles only
   pairs                     the Verlet pair set within r_cut + r_skin (Sec. 2.1.2)
@@ -40,6 +42,7 @@ class OrcSystem(C.Structure):
         ("bonds", C.POINTER(C.c_int32)),
         ("fene_K", C.c_double),
         ("fene_R0", C.c_double),
+        ("pot", C.c_int32),
     ]
 
 
@@ -54,6 +57,10 @@ def lib():
         L.orc_lj_energy.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_lj_force.restype = C.c_double
         L.orc_lj_force.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_soft_energy.restype = C.c_double
+        L.orc_soft_energy.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_soft_force.restype = C.c_double
+        L.orc_soft_force.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_min_image_r2.restype = C.c_double
         L.orc_min_image_r2.argtypes = [dp, dp, dp]
         L.orc_forces.restype = C.c_int
@@ -99,11 +106,13 @@ class System:
 
     rc is absolute (for the LJ fluid 2.5 sigma; for WCA 2**(1/6) sigma).
     shift=True subtracts V(rc) so the pair energy is continuous at the cutoff.
+    soft=True replaces the LJ pair by the cosine push-off A (1 + cos(pi r / rc))
+    with A = eps (sigma and shift unused).
     """
 
     def __init__(self, n, box, eps=1.0, sigma=1.0, rc=2.5, shift=True, mass=1.0,
                  dt=0.005, gamma=0.0, kT=1.0, seed=0, bonds=None, fene_K=30.0,
-                 fene_R0=1.5):
+                 fene_R0=1.5, soft=False):
         self.n = int(n)
         box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)).copy()
         self.box = box
@@ -111,6 +120,7 @@ class System:
         self.mass, self.dt, self.gamma, self.kT, self.seed = float(mass), float(dt), float(gamma), float(kT), int(seed)
         self.bonds = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
         self.fene_K, self.fene_R0 = float(fene_K), float(fene_R0)
+        self.soft = bool(soft)
 
     def c(self):
         s = OrcSystem()
@@ -126,6 +136,7 @@ class System:
             s.n_bonds = 0
             s.bonds = C.POINTER(C.c_int32)()
         s.fene_K, s.fene_R0 = self.fene_K, self.fene_R0
+        s.pot = 1 if self.soft else 0
         return s
 
 
@@ -135,6 +146,14 @@ def lj_energy(r, eps=1.0, sigma=1.0):
 
 def lj_force(r, eps=1.0, sigma=1.0):
     return lib().orc_lj_force(float(r), float(eps), float(sigma))
+
+
+def soft_energy(r, A=1.0, rc=2 ** (1 / 6)):
+    return lib().orc_soft_energy(float(r), float(A), float(rc))
+
+
+def soft_force(r, A=1.0, rc=2 ** (1 / 6)):
+    return lib().orc_soft_force(float(r), float(A), float(rc))
 
 
 def min_image_r2(xi, xj, box):

@@ -23,7 +23,10 @@
  *   - the Langevin thermostat is a force term -gamma m v + sqrt(24 gamma kT m/dt) u,
  *     u uniform in (-1/2, 1/2) from Philox4x32-10 keyed by (seed) and counted by
  *     (particle id, step), applied with the velocity available at force time;
- *   - minimum image d -= L * nearbyint(d / L) per axis (valid for L >= 2 r_cut).
+ *   - minimum image d -= L * nearbyint(d / L) per axis (valid for L >= 2 r_cut);
+ *   - the soft push-off used to prepare overlapping polymer chains before the
+ *     WCA melt run (Sec. 4 names the melt, not its preparation) is the cosine
+ *     potential V = A (1 + cos(pi r / r_cut)) for r < r_cut, with A = eps.
  *
  * Layout: positions, velocities and forces are row-major N x 3 arrays
  * (x0, y0, z0, x1, ...).  All arithmetic is IEEE FP64; build with
@@ -31,6 +34,9 @@
  * which makes the squared distance below a fixed, reproducible function of
  * the two positions.
  */
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -55,6 +61,7 @@ typedef struct {
     int64_t n_bonds;      /* FENE bonds                                  */
     const int32_t *bonds; /* 2*n_bonds particle ids, or NULL             */
     double fene_K, fene_R0;
+    int32_t pot;          /* 0: LJ / WCA (Eq. 2), 1: soft cosine push-off  */
 } orc_system;
 
 enum { ORC_OK = 0, ORC_ERR_BOND = -5, ORC_ERR_CAP = -3, ORC_ERR_ARG = -1 };
@@ -104,10 +111,32 @@ double orc_min_image_r2(const double *xi, const double *xj, const double *box)
     return min_image(xi, xj, box, d);
 }
 
+/* Soft cosine push-off V(r) = A (1 + cos(pi r / rc)) for r < rc: V(0) = 2A,
+ * V(rc) = 0 and dV/dr(rc) = 0.  Its force -dV/dr = (pi A / rc) sin(pi r / rc)
+ * is bounded by pi A / rc, so fully overlapping beads can be separated. */
+double orc_soft_energy(double r, double A, double rc)
+{
+    return A * (1.0 + cos(M_PI * r / rc));
+}
+
+double orc_soft_force(double r, double A, double rc)
+{
+    return M_PI * A / rc * sin(M_PI * r / rc);
+}
+
 /* Pair force on i from j and pair energy for separation d (r2 = |d|^2 < rc^2). */
 static void lj_pair(const orc_system *s, const double d[3], double r2,
                     double f[3], double *v_pair, double *w_pair)
 {
+    if (s->pot == 1) {
+        double r = sqrt(r2);
+        double fmag = orc_soft_force(r, s->eps, s->rc);
+        /* coincident particles: V = 2A, no direction, no force */
+        for (int k = 0; k < 3; ++k) f[k] = r > 0.0 ? fmag * d[k] / r : 0.0;
+        *v_pair = orc_soft_energy(r, s->eps, s->rc);
+        *w_pair = d[0] * f[0] + d[1] * f[1] + d[2] * f[2];
+        return;
+    }
     double r = sqrt(r2);
     double fmag = orc_lj_force(r, s->eps, s->sigma);  /* -dV/dr */
     double v = orc_lj_energy(r, s->eps, s->sigma);

@@ -503,17 +503,37 @@ __host__ __device__ inline size_t list_smem_bytes(int hcap)
 // r_skin) away and fails the distance test, so each list is exactly the pair
 // set, ordered by halo row and slot.  Distances in fixed-point units of the
 // x axis (see Replica).
-// One candidate batch of the list walk: squared separations of 4 halo
-// entries from this lane's particle in x-axis units.
-template <bool CUBIC>
-__device__ __forceinline__ float sep2(uint4 p, uint4 q, float ry, float rz)
-{
-    float d0 = (float)(int)(p.x - q.x);
-    float d1 = (float)(int)(p.y - q.y);
-    float d2 = (float)(int)(p.z - q.z);
-    if (!CUBIC) { d1 *= ry; d2 *= rz; }
-    return d0 * d0 + d1 * d1 + d2 * d2;
-}
+// Halo entries of the list walk, in one of two forms.
+// Relative (REL): FP32 coordinates relative to the tile centre in x-axis
+// fixed-point units, w = the halo index.  With at least 3 cells in y and z
+// and a tile at least 3 cells narrower than its row, no halo coordinate wraps
+// around the centre (offsets stay below L / 2) and every tile-halo pair spans
+// less than L - r_list along each axis, so the difference of two entries is
+// the minimum image wherever that can be below r_list.  It saves the
+// per-candidate integer-to-float conversions.
+// Absolute: the fixed-point positions; the int32 difference is the minimum
+// image in every case.
+template <bool REL> struct Cand;
+template <> struct Cand<true> {
+    using T = float4;
+    __device__ static float sep2(const float4 &p, const float4 &q, float, float)
+    {
+        const float d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z;
+        return d0 * d0 + d1 * d1 + d2 * d2;
+    }
+    __device__ static int index(const float4 &q, int) { return __float_as_int(q.w); }
+};
+template <> struct Cand<false> {
+    using T = uint4;
+    __device__ static float sep2(const uint4 &p, const uint4 &q, float ry, float rz)
+    {
+        const float d0 = (float)(int)(p.x - q.x);
+        const float d1 = (float)(int)(p.y - q.y) * ry;
+        const float d2 = (float)(int)(p.z - q.z) * rz;
+        return d0 * d0 + d1 * d1 + d2 * d2;
+    }
+    __device__ static int index(const uint4 &, int h) { return h; }
+};
 
 // Verlet lists of one tile (Sec. 2.1.2): each warp takes 32 consecutive
 // particles and walks the union of their 27-cell stencils, candidate by
@@ -524,18 +544,21 @@ __device__ __forceinline__ float sep2(uint4 p, uint4 q, float ry, float rz)
 // row and the row pointer advances only on a hit.  The shared stage has the
 // final [row][particle] layout of the tile's list block; a list that outgrows
 // it is walked again straight into global memory (rare).
-template <bool CUBIC>
+template <bool REL>
 __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
-                                              const uint4 *halo, unsigned short *lst, const double *X, int hfirst,
-                                              int *s_kmax, int &mx, long long &sm, int &err)
+                                              const typename Cand<REL>::T *halo, unsigned short *lst, const double *X,
+                                              int hfirst, int *s_kmax, int &mx, long long &sm, int &err)
 {
+    using C = Cand<REL>;
+    using T = typename C::T;
+    const float ry = R.ry, rz = R.rz;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
     int ly, cntY, lz, cntZ;
     axis_offsets(ny, ly, cntY);
     axis_offsets(nz, lz, cntZ);
     const int nrow = cntY * cntZ;
-    const float lo = R.rl2_lo_u, hi = R.rl2_hi_u, ry = R.ry, rz = R.rz;
+    const float lo = R.rl2_lo_u, hi = R.rl2_hi_u;
     const int Pt = tl.s1 - tl.s0;
     // stage rows of this tile (0: no stage, every list goes to global memory)
     const int cap = Pt <= kTileMax ? min((kListStage * kTileMax) / max(Pt, 1), b.K) : 0;
@@ -575,7 +598,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             }
         }
         const int self = valid ? hfirst + pp : -1;
-        const uint4 p = halo[hfirst + (valid ? pp : c0)];
+        const T p = halo[hfirst + (valid ? pp : c0)];
         // this lane's stage column (row stride Pt); lanes without one write a
         // private dummy slot (stride 0)
         const bool own = valid && cap > 0;
@@ -587,7 +610,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             const int j0 = __shfl_sync(0xffffffffu, rj0, r);
             int h = h0;
             for (; h + 4 <= h1; h += 4) {
-                uint4 pj[4];
+                T pj[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) pj[u] = halo[h + u];
                 float r2[4];
@@ -595,8 +618,8 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 bool bnd = false;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    r2[u] = sep2<CUBIC>(p, pj[u], ry, rz);
-                    in[u] = (r2[u] < lo) & (h + u != self);
+                    r2[u] = C::sep2(p, pj[u], ry, rz);
+                    in[u] = (r2[u] < lo) & (C::index(pj[u], h + u) != self);
                     bnd |= (r2[u] < hi) & !(r2[u] < lo);
                 }
                 if (__any_sync(0xffffffffu, bnd)) {
@@ -609,13 +632,13 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 unsigned short *q = col + max(min(cnt, cap - 4), 0) * stride;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    *q = (unsigned short)(h + u);
+                    *q = (unsigned short)C::index(pj[u], h + u);
                     q += in[u] ? stride : 0;
                     cnt += in[u];
                 }
             }
             for (; h < h1; ++h) {
-                const float r2 = sep2<CUBIC>(p, halo[h], ry, rz);
+                const float r2 = C::sep2(p, halo[h], ry, rz);
                 const bool mine = valid & (h != self);
                 bool in = (r2 < lo) & mine;
                 const bool band = (r2 < hi) & !(r2 < lo) & mine;
@@ -628,14 +651,14 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         // a list longer than the stage allows (or a tile without a stage):
         // walk the candidates again; rows below cap go to the stage, the rest
         // to global memory
-        const bool over = valid && (cnt > cap - 4);
+    const bool over = valid && (cnt > cap - 4);
         if (__any_sync(0xffffffffu, over)) {
             int c2 = 0;
             for (int r = 0; r < nrow * 2; ++r) {
                 const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
                 const int j0 = __shfl_sync(0xffffffffu, rj0, r);
                 for (int h = h0; h < h1; ++h) {
-                    const float r2 = sep2<CUBIC>(p, halo[h], ry, rz);
+                    const float r2 = C::sep2(p, halo[h], ry, rz);
                     const bool mine = valid & (h != self);
                     bool in = (r2 < lo) & mine;
                     if ((r2 < hi) & !(r2 < lo) & mine) in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
@@ -667,6 +690,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
     extern __shared__ uint4 halo[];
+    float4 *halof = reinterpret_cast<float4 *>(halo);                          // the same entries, converted
     unsigned short *lst = reinterpret_cast<unsigned short *>(halo + b.hcap);   // [k][Pt] stage, then 32 dummy slots
     __shared__ Piece pc[kMaxPieces + 1];
     __shared__ Tile tl;
@@ -702,8 +726,22 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
         stage_halo<uint4>(pc, s_np, [&](int h, int j) { cp_async16(&halo[h], &P[j]); });
         cp_async_wait_all();
         __syncthreads();
+        const bool rel = R.ncell[1] >= 3 && R.ncell[2] >= 3 && tl.x1 - tl.x0 <= R.ncell[0] - 3;
+        if (rel) {
+            // FP32 coordinates relative to the tile centre (exact integer
+            // minimum image, one rounding), y and z in x-axis units
+            const unsigned cx = (unsigned)((((unsigned long long)(tl.x0 + tl.x1)) << 31) / (unsigned)R.ncell[0]);
+            const unsigned cy = (unsigned)((((unsigned long long)(2 * tl.cy + 1)) << 31) / (unsigned)R.ncell[1]);
+            const unsigned cz = (unsigned)((((unsigned long long)(2 * tl.cz + 1)) << 31) / (unsigned)R.ncell[2]);
+            for (int h = threadIdx.x; h < H; h += blockDim.x) {
+                const uint4 q = halo[h];
+                halof[h] = make_float4((float)(int)(q.x - cx), (float)(int)(q.y - cy) * R.ry,
+                                       (float)(int)(q.z - cz) * R.rz, __int_as_float(h));
+            }
+        }
+        __syncthreads();
         const int hfirst = tile_self_offset(R, tl, pc, s_np);
-        if (R.cubic) cells_of_tile<true>(b, R, tl, pc, s_np, halo, lst, X, hfirst, &s_kmax, mx, sm, err);
+        if (rel) cells_of_tile<true>(b, R, tl, pc, s_np, halof, lst, X, hfirst, &s_kmax, mx, sm, err);
         else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, &s_kmax, mx, sm, err);
         __syncthreads();
         if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;

@@ -14,6 +14,8 @@
 //     from the master positions, so the interacting set is the FP64 set.
 //   FP64: the same sums in double precision from the master positions.
 // Positions and velocities are integrated in FP64 in both precisions.
+#include <math_constants.h>
+
 #include "md_internal.cuh"
 
 namespace mdk {
@@ -448,7 +450,21 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                     if (r2 < rc2 + band) {
                         bool in = r2 < rc2 - band;
                         if (!in) in = r2_exact(X, b.S, i, halo_slot(pc, np, h), R.L) < rc2;
-                        if (in) {
+                        if (in && R.soft) {
+                            // cosine push-off A (1 + cos(pi r / r_cut)), A = eps:
+                            // -dV/dr = (pi A / r_cut) sin(pi r / r_cut), none at r = 0
+                            const double r = sqrt(r2);
+                            double sn, cs;
+                            sincospi(r / R.rc, &sn, &cs);
+                            const double fs = r > 0.0 ? (CUDART_PI * R.eps / R.rc) * sn / r : 0.0;
+                            Fd[0] += fs * dx;
+                            Fd[1] += fs * dy;
+                            Fd[2] += fs * dz;
+                            if (ENERGY) {
+                                ui += 0.5 * (R.eps * (1.0 + cs));
+                                wi += 0.5 * fs * r2;
+                            }
+                        } else if (in) {
                             const double ir2 = 1.0 / r2;
                             const double s2 = sig2 * ir2;
                             const double s6 = s2 * s2 * s2;

@@ -305,9 +305,11 @@ md_status md_create(const md_params *p, md_handle **out)
     if (!p || p->n_replicas < 1 || p->n_replicas > mdk::kMaxReplicas || !p->replica_offsets || !p->box ||
         !p->eps || !p->sigma)
         return MD_ERR_ARG;
-    if (!(p->dt > 0) || !(p->mass > 0) || !(p->skin >= 0) || (p->potential != MD_LJ && p->potential != MD_WCA) ||
+    if (!(p->dt > 0) || !(p->mass > 0) || !(p->skin >= 0) ||
+        (p->potential != MD_LJ && p->potential != MD_WCA && p->potential != MD_SOFT) ||
         (p->precision != MD_FP64 && p->precision != MD_FP32_FIXED) || p->langevin_gamma < 0 ||
-        (p->potential == MD_LJ && !(p->rc_over_sigma > 0)) || p->list_capacity < 0 || p->n_bonds < 0 ||
+        (p->potential != MD_WCA && !(p->rc_over_sigma > 0)) ||
+        (p->potential == MD_SOFT && p->precision != MD_FP64) || p->list_capacity < 0 || p->n_bonds < 0 ||
         (p->n_bonds > 0 && (!p->bonds || !(p->fene_K > 0) || !(p->fene_R0 > 0))) ||
         (p->langevin_gamma > 0 && !(p->kT >= 0)))
         return MD_ERR_ARG;
@@ -361,7 +363,8 @@ md_status md_create(const md_params *p, md_handle **out)
         R.sigma = sig;
         R.rc = rc;
         R.rc2 = rc * rc;
-        R.vshift = lj_v(rc, eps, sig);
+        R.soft = p->potential == MD_SOFT ? 1 : 0;
+        R.vshift = R.soft ? 0.0 : lj_v(rc, eps, sig);
         R.rl2 = rl * rl;
         R.eps24_f = (float)(24.0 * eps);
         R.eps4_f = (float)(4.0 * eps);
@@ -372,7 +375,9 @@ md_status md_create(const md_params *p, md_handle **out)
         // fixed-point quantisation (|dd| <= sqrt(3) L / 2^32) plus FP32 rounding
         const double qd = std::sqrt(3.0) * Lmax / 4294967296.0;
         const double brc = 2.0 * rc * qd + std::ldexp(1.0, -16) * rc * rc;
-        const double brl = 2.0 * rl * qd + std::ldexp(1.0, -16) * rl * rl;
+        // the list walk rounds coordinates relative to the tile centre (|c| <= L / 2)
+        // to FP32: up to L / 2^24 more per separation component
+        const double brl = 2.0 * rl * (qd + std::sqrt(3.0) * Lmax / 16777216.0) + std::ldexp(1.0, -16) * rl * rl;
         R.rc2_lo = (float)(rc * rc - brc);
         R.rc2_hi = (float)(rc * rc + brc);
         R.rl2_lo = (float)(rl * rl - brl);
@@ -754,8 +759,8 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
 {
     if (!h || nsteps < 0 || ckpt_every < 1) return fail(h, MD_ERR_ARG, "md_forward: bad arguments");
     if (!h->state_set) return fail(h, MD_ERR_ARG, "md_forward before md_set_state");
-    if (h->b.has_bonds || h->b.langevin)
-        return fail(h, MD_ERR_ARG, "md_forward: the adjoint covers NVE pair potentials only (no bonds, no thermostat)");
+    if (h->b.has_bonds || h->b.langevin || h->p.potential == MD_SOFT)
+        return fail(h, MD_ERR_ARG, "md_forward: the adjoint covers NVE LJ / WCA pair forces only (no bonds, thermostat or push-off)");
     cudaStream_t st = (cudaStream_t)stream;
     const long long n6 = 6LL * h->N;
     const long long nck = nsteps / ckpt_every + 1;

@@ -61,6 +61,7 @@ struct Replica {
     // pair potential (Eq. 2), FP64 and FP32 copies
     double eps, sigma, rc, rc2, vshift;   // vshift = V(rc) (0 shift for none)
     double rl2;                           // (r_cut + r_skin)^2
+    int soft;                             // cosine push-off instead of Eq. 2 (FP64 path only)
     float eps24_f, sig2_f, rc2_f, vshift_f, eps4_f;
     float rc2_lo, rc2_hi;                 // FP32 band around rc^2 resolved in FP64
     float rl2_lo, rl2_hi;                 // FP32 band around (r_cut + r_skin)^2

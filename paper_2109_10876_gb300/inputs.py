@@ -280,3 +280,24 @@ def ensemble(nrep=64, nmin=500, nmax=32000, rho=0.8442, T=0.72, seed=11,
         vs.append(v)
         boxes.append(box)
     return sizes, np.array(boxes), eps, sig, np.concatenate(xs), np.concatenate(vs)
+
+
+def melt(nchain=2000, nbead=200, rho=0.85, T=1.0, seed=4, bond=0.97):
+    """Linear bead-spring chains for the polymer melt (Sec. 4): nchain chains
+    of nbead beads at bead density rho in a cubic box, each a free random
+    walk of fixed bond length `bond` from a uniform random start (overlaps are
+    left for the soft push-off to remove); Gaussian velocities at T.
+    Returns (x (N, 3), v (N, 3), box (3,), bonds (nchain (nbead - 1), 2))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = nchain * nbead
+    L = (n / rho) ** (1.0 / 3.0)
+    box = np.array([L, L, L])
+    start = rng.uniform(0.0, L, size=(nchain, 1, 3))
+    u = rng.standard_normal((nchain, nbead - 1, 3))
+    u *= bond / np.linalg.norm(u, axis=2, keepdims=True)
+    walk = np.concatenate([np.zeros((nchain, 1, 3)), np.cumsum(u, axis=1)], axis=1)
+    x = wrap((start + walk).reshape(-1, 3), box)
+    first = (np.arange(nchain)[:, None] * nbead + np.arange(nbead - 1)[None, :]).ravel()
+    bonds = np.stack([first, first + 1], axis=1).astype(np.int32)
+    v = maxwell_velocities(n, T, seed + 31)
+    return x, v, box, bonds

@@ -30,7 +30,7 @@ MD_ERR_BOX_TOO_SMALL = -8
 STATUS_NAMES = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_CUDA", -3: "MD_ERR_LIST_OVERFLOW",
                 -4: "MD_ERR_NONFINITE", -5: "MD_ERR_BOND_BROKEN", -6: "MD_ERR_FIXED_OVERFLOW",
                 -7: "MD_ERR_TIMEOUT", -8: "MD_ERR_BOX_TOO_SMALL"}
-MD_LJ, MD_WCA = 0, 1
+MD_LJ, MD_WCA, MD_SOFT = 0, 1, 2
 MD_SECT_NEIGH, MD_SECT_FORCE, MD_SECT_OTHER, MD_NSECT = 0, 1, 2, 3
 MD_FP64, MD_FP32_FIXED = 0, 1
 

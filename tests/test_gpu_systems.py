@@ -163,3 +163,40 @@ def test_slab_forces_and_pairs(md, precision):
     np.testing.assert_allclose(euw.cpu().numpy(), er, rtol=TOL[precision], atol=TOL[precision] * n)
     want, _ = oracle.pairs(s, x, 2.8)
     np.testing.assert_array_equal(md.export_pairs_sorted(h), want)
+
+
+def test_soft_pushoff_fene_langevin_fp64(md):
+    """Melt preparation: free random-walk chains (overlapping beads, some
+    coincident) under the cosine push-off with FENE bonds and the Langevin
+    thermostat.  Forces and energies match the oracle at the start, and 20
+    steps follow the oracle's trajectory."""
+    x, v, box, bonds = inputs.melt(nchain=10, nbead=20, rho=0.85, seed=41)
+    n = len(x)
+    rc = 2 ** (1 / 6)
+    kw = dict(potential=md.MD_SOFT, rc_over_sigma=rc, eps=5.0, skin=0.4, bonds=bonds, fene_K=30.0,
+              fene_R0=1.5, dt=0.005, langevin_gamma=0.5, kT=1.0, seed=77)
+    h = md.md_create(n, box, precision=0, **kw)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    f = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+    euw = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, euw)
+    md.md_sync(h)
+    s = oracle.System(n, box, eps=5.0, rc=rc, soft=True, bonds=bonds, fene_K=30.0, fene_R0=1.5, dt=0.005,
+                      gamma=0.5, kT=1.0, seed=77)
+    Fo, eo = oracle.forces(s, x, v)
+    assert force_rel_err(host(f), Fo) <= 1e-12
+    np.testing.assert_allclose(euw.cpu().numpy()[0], eo, rtol=1e-12, atol=1e-12 * n)
+    md.md_step(h, 20)
+    xo = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+    vo = torch.zeros_like(xo)
+    md.md_get_state(h, xo, vo)
+    x1, v1, _ = oracle.vv_run(s, x, v, 20)
+    assert np.max(np.abs(min_image_diff(host(xo), x1, box))) < 1e-10
+    assert np.max(np.abs(host(vo) - v1)) < 1e-9
+
+
+def test_soft_pushoff_needs_fp64(md):
+    x, v, box, bonds = inputs.melt(nchain=4, nbead=10, rho=0.85, seed=42)
+    with pytest.raises(md.MDError):
+        md.md_create(len(x), box, potential=md.MD_SOFT, rc_over_sigma=2 ** (1 / 6), precision=1)

@@ -368,3 +368,59 @@ def test_adjoint_initial_state_gradient():
         fv = (_loss(x, v + h * dv, box, 1, 1, 4, 2.5, *c) - _loss(x, v - h * dv, box, 1, 1, 4, 2.5, *c)) / (2 * h)
         assert np.sum(lx * dx) == pytest.approx(fx, rel=1e-5)
         assert np.sum(lv * dv) == pytest.approx(fv, rel=1e-5)
+
+
+# ---------------------------------------------------------------- soft push-off
+def test_soft_pushoff_closed_forms_and_derivative():
+    """Cosine push-off A (1 + cos(pi r / rc)): V(0) = 2A, V(rc/2) = A, V(rc) = 0;
+    the force is the sympy derivative -dV/dr, pi A / rc at rc / 2 and zero at
+    0 and rc (continuous at the cutoff); coincident beads feel no force."""
+    rc = 2 ** (1 / 6)
+    for A in (1.0, 7.5, 100.0):
+        assert oracle.soft_energy(0.0, A, rc) == pytest.approx(2 * A, rel=1e-15)
+        assert oracle.soft_energy(0.5 * rc, A, rc) == pytest.approx(A, rel=1e-14)
+        assert abs(oracle.soft_energy(rc, A, rc)) < 1e-14 * A
+        assert oracle.soft_force(0.5 * rc, A, rc) == pytest.approx(math.pi * A / rc, rel=1e-14)
+        assert abs(oracle.soft_force(rc, A, rc)) < 1e-13 * A
+        assert oracle.soft_force(0.0, A, rc) == 0.0
+    r, a, c = sp.symbols("r a c", positive=True)
+    V = a * (1 + sp.cos(sp.pi * r / c))
+    dV = sp.lambdify((r, a, c), -sp.diff(V, r), "mpmath")
+    for rr in np.linspace(0.05, 1.1, 23):
+        assert oracle.soft_force(rr, 3.0, rc) == pytest.approx(float(dV(rr, 3.0, rc)), rel=1e-12, abs=1e-13)
+    box = np.array([4.0, 4.0, 4.0])
+    x = np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 1.0], [1.3, 1.0, 1.0]])
+    s = oracle.System(3, box, eps=2.0, rc=rc, soft=True)
+    F, euw = oracle.forces(s, x)
+    f01 = oracle.soft_force(0.3, 2.0, rc)          # j = 2 pushes 0 and 1 towards -x
+    np.testing.assert_allclose(F[0], [-f01, 0, 0], rtol=1e-14)
+    np.testing.assert_allclose(F[1], [-f01, 0, 0], rtol=1e-14)
+    np.testing.assert_allclose(F[2], [2 * f01, 0, 0], rtol=1e-14)
+    assert euw[0] == pytest.approx(2 * 2.0 + 2 * oracle.soft_energy(0.3, 2.0, rc), rel=1e-14)
+
+
+def test_soft_pushoff_force_is_minus_grad_U_and_nve_second_order():
+    """On a random gas: forces are -grad U by central differences, Newton's
+    third law holds, and velocity Verlet conserves energy to second order."""
+    box = np.array([6.0, 6.0, 6.0])
+    x = inputs.random_gas(300, box, seed=21)
+    n = len(x)
+    s = oracle.System(n, box, eps=5.0, rc=2 ** (1 / 6), soft=True)
+    F, euw = oracle.forces(s, x)
+    assert np.max(np.abs(F.sum(axis=0))) < 1e-12 * np.max(np.abs(F)) * n
+    h = 1e-6
+    for i in np.random.default_rng(3).choice(n, 5, replace=False):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            d = -(oracle.forces(s, xp)[1][0] - oracle.forces(s, xm)[1][0]) / (2 * h)
+            assert F[i, k] == pytest.approx(d, abs=1e-6 * max(1.0, abs(F[i, k])))
+    v = inputs.maxwell_velocities(n, 1.0, 22)
+    dE = []
+    for dt in (0.004, 0.002):
+        s = oracle.System(n, box, eps=5.0, rc=2 ** (1 / 6), soft=True, dt=dt)
+        e0 = oracle.forces(s, x, v)[1]
+        th = oracle.vv_run(s, x, v, int(round(0.4 / dt)), thermo=True)[3]
+        dE.append(np.max(np.abs(th[:, 0] + th[:, 1] - e0[0] - e0[1])))
+    assert 3.0 < dE[0] / dE[1] < 5.0
