@@ -39,6 +39,9 @@ RHO, T0, RC, SKIN, DT = 0.8442, 0.72, 2.5, 0.3, 0.005
 # besides the list: own fixed-point position 16, list length 4, x read+write 48,
 # v read+write 48, new fixed-point position 16, build-time position 16
 FORCE_FIXED_BYTES = 16 + 4 + 48 + 48 + 16 + 16
+# kernels of one list rebuild: bin, 3-phase scan, scatter, reorder, tile count /
+# scan / write / pieces, list build
+REBUILD_KERNELS = 11
 
 
 def parse():
@@ -263,7 +266,7 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+fixed64 (f64 integration)", "data": "synthetic",
             "config": dict(extra, particles=n, tile_size=st1["tile_size"]),
-            "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + 9 * rb,
+            "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + REBUILD_KERNELS * rb,
             "mean_list_len": st1["list_entries"] / n, "max_list_len": st1["max_list_len"],
             "max_cell_occupancy": st1["max_cell_occupancy"], "tiles": st1["n_tiles"],
             "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck}
@@ -527,7 +530,7 @@ def main():
                            "l2": "working set larger than L2 (positions, velocities and the Verlet list: "
                                  f"~{(n * (FORCE_FIXED_BYTES + list_bytes)) / 1e6:.0f} MB touched per step)"},
                 "roofline": roofline,
-                "gpu_launches": 2 * args.steps + 3 + 9 * (st1["rebuilds"] - st0["rebuilds"]),
+                "gpu_launches": 2 * args.steps + 3 + REBUILD_KERNELS * (st1["rebuilds"] - st0["rebuilds"]),
                 "rebuilds": st1["rebuilds"] - st0["rebuilds"],
                 "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / args.steps,
                                          "force_integrate": sect_ms[md.MD_SECT_FORCE] / args.steps,

@@ -160,6 +160,11 @@ __global__ void k_set_steps(Ctl *ctl, long long left) { ctl->steps_left = left; 
 __global__ void k_bin(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        b.ctl->max_nn = 0;
+        b.ctl->list_entries = 0;
+        b.ctl->max_occ = 0;
+    }
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.S) return;
     uint4 p = b.pos[b.ctl->cur][s];
@@ -172,8 +177,6 @@ __global__ void k_bin(Bufs b)
     atomicAdd(&b.cell_count[c], 1);
 }
 
-// Exclusive scan of the histogram, per replica, offset by the replica's first
-// slot.  One block of 1024 threads; each thread scans a contiguous chunk.
 constexpr int kScanThreads = 1024;
 
 __device__ int block_excl_scan(int v, int *warp_sums, int &total)
@@ -205,38 +208,53 @@ __device__ int block_excl_scan(int v, int *warp_sums, int &total)
     return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan(Bufs b)
+// The cell scan in three phases over blocks of kScanBlock cells: block sums
+// (and the largest occupancy), an exclusive scan of the block sums, then each
+// block's exclusive scan plus its offset.  Each replica's padding slots count
+// after its last cell, so the result is the first slot of every cell.
+__global__ void __launch_bounds__(kScanBlock) k_scan_sum(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
     __shared__ int warp_sums[33];
-    if (threadIdx.x == 0) {
-        b.ctl->max_nn = 0;
-        b.ctl->list_entries = 0;
-        b.ctl->max_occ = 0;
-    }
-    int local_max = 0;
-    for (int r = 0; r < b.nrep; ++r) {
-        const Replica &R = b.rep[r];
-        int n = R.ncells;
-        int chunk = (n + kScanThreads - 1) / kScanThreads;
-        int lo = min(n, (int)threadIdx.x * chunk), hi = min(n, lo + chunk);
-        int sum = 0;
-        for (int c = lo; c < hi; ++c) {
-            int k = b.cell_count[R.cell_off + c];
-            sum += k;
-            local_max = max(local_max, k);
-        }
+    const int c = blockIdx.x * kScanBlock + threadIdx.x;
+    const int k = c < b.C ? b.cell_count[c] : 0;
+    const int v = c < b.C ? k + b.cell_pad[c] : 0;
+    int total;
+    block_excl_scan(v, warp_sums, total);
+    if (threadIdx.x == 0) b.scan_part[blockIdx.x] = total;
+    int m = k;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&b.ctl->max_occ, m);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    __shared__ int warp_sums[33];
+    const int nb = (b.C + kScanBlock - 1) / kScanBlock;
+    int carry = 0;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int q = base + (int)threadIdx.x;
+        const int v = q < nb ? b.scan_part[q] : 0;
         int total;
-        int base = block_excl_scan(sum, warp_sums, total) + (int)R.slot_begin;
-        for (int c = lo; c < hi; ++c) {
-            int k = b.cell_count[R.cell_off + c];
-            b.cell_start[R.cell_off + c] = base;
-            b.cell_end[R.cell_off + c] = base;   // cursor for the scatter
-            base += k;
-        }
+        const int e = block_excl_scan(v, warp_sums, total);
+        if (q < nb) b.scan_part[q] = carry + e;
+        carry += total;
     }
-    for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&b.ctl->max_occ, local_max);
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_write(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    __shared__ int warp_sums[33];
+    const int c = blockIdx.x * kScanBlock + threadIdx.x;
+    const int v = c < b.C ? b.cell_count[c] + b.cell_pad[c] : 0;
+    int total;
+    const int e = block_excl_scan(v, warp_sums, total) + b.scan_part[blockIdx.x];
+    if (c < b.C) {
+        b.cell_start[c] = e;
+        b.cell_end[c] = e;   // cursor for the scatter
+    }
 }
 
 // Scatter each particle's old slot into its cell's bucket (order within a
@@ -252,9 +270,28 @@ __global__ void k_scatter(Bufs b)
     b.bucket[k] = (int)s;
 }
 
-// One warp per cell: order the cell's members by particle id (so the slot
-// order is a function of the positions alone), then gather x, v, pos from
-// buffer cur into buffer cur ^ 1 at the new slots.
+// One warp per cell: order the cell's members by (fixed-point x, particle
+// id), a function of the positions alone, so that every row of cells is
+// sorted along x; then gather x, v, pos from buffer cur into buffer cur ^ 1
+// at the new slots.  Ranks come from warp shuffles for cells of up to 32.
+__device__ __forceinline__ unsigned long long order_key(uint4 p)
+{
+    return ((unsigned long long)p.x << 32) | (unsigned)p.w;
+}
+
+__device__ __forceinline__ void reorder_move(const Bufs &b, int cur, int nxt, int c, int s, int dst, uint4 p)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        b.x[nxt][k * b.S + dst] = b.x[cur][k * b.S + s];
+        b.v[nxt][k * b.S + dst] = b.v[cur][k * b.S + s];
+    }
+    b.pos[nxt][dst] = p;
+    b.xref[dst] = p;
+    b.slot_of_id[(int)p.w] = dst;
+    b.cellid[dst] = c;
+}
+
 __global__ void k_reorder(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
@@ -267,25 +304,23 @@ __global__ void k_reorder(Bufs b)
     if (lane == 0) b.cell_count[c] = 0;   // histogram is clean for the next build
     int cur = b.ctl->cur, nxt = cur ^ 1;
     const uint4 *pin = b.pos[cur];
+    if (n <= 32) {
+        const bool act = lane < n;
+        const int s = act ? b.bucket[start + lane] : 0;
+        const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
+        const unsigned long long key = act ? order_key(p) : ~0ULL;
+        int rank = 0;
+        for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, key, q) < key);
+        if (act) reorder_move(b, cur, nxt, c, s, start + rank, p);
+        return;
+    }
     for (int m = lane; m < n; m += 32) {
         int s = b.bucket[start + m];
         uint4 p = pin[s];
-        int id = (int)p.w;
+        const unsigned long long key = order_key(p);
         int rank = 0;
-        for (int q = 0; q < n; ++q) {
-            int o = (int)pin[b.bucket[start + q]].w;
-            rank += (o < id);
-        }
-        int dst = start + rank;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            b.x[nxt][k * b.S + dst] = b.x[cur][k * b.S + s];
-            b.v[nxt][k * b.S + dst] = b.v[cur][k * b.S + s];
-        }
-        b.pos[nxt][dst] = p;
-        b.xref[dst] = p;
-        b.slot_of_id[id] = dst;
-        b.cellid[dst] = c;
+        for (int q = 0; q < n; ++q) rank += (order_key(pin[b.bucket[start + q]]) < key);
+        reorder_move(b, cur, nxt, c, s, start + rank, p);
     }
 }
 
@@ -597,6 +632,30 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 if (rh0 < pc[qq].hoff || rh1 > pc[qq].hoff + pc[qq].n) { err |= kErrList; rh1 = rh0; }
             }
         }
+        if constexpr (REL) {
+            // Rows are sorted along x (cells in order, members by x), and so
+            // are the warp's own particles: candidates farther along x than
+            // the window from the first and last of them are out of reach of
+            // all 32.  Each range is trimmed by two binary searches.
+            const float xlo = halo[hfirst + c0].x - R.rl_win_u;
+            const float xhi = halo[hfirst + min(c0 + 31, Pt - 1)].x + R.rl_win_u;
+            if (rh1 > rh0) {
+                int a = rh0, e = rh1;
+                while (a < e) {
+                    const int m = (a + e) >> 1;
+                    if (halo[m].x < xlo) a = m + 1; else e = m;
+                }
+                int a2 = a;
+                e = rh1;
+                while (a2 < e) {
+                    const int m = (a2 + e) >> 1;
+                    if (halo[m].x <= xhi) a2 = m + 1; else e = m;
+                }
+                rj0 += a - rh0;
+                rh0 = a;
+                rh1 = a2;
+            }
+        }
         const int self = valid ? hfirst + pp : -1;
         const T p = halo[hfirst + (valid ? pp : c0)];
         // this lane's stage column (row stride Pt); lanes without one write a
@@ -863,7 +922,10 @@ static int list_grid(size_t smem)
 void launch_rebuild_chain(const Bufs &b, cudaStream_t st)
 {
     k_bin<<<b.nblk, kBlock, 0, st>>>(b);
-    k_scan<<<1, kScanThreads, 0, st>>>(b);
+    const unsigned nsb = (unsigned)((b.C + kScanBlock - 1) / kScanBlock);
+    k_scan_sum<<<nsb, kScanBlock, 0, st>>>(b);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(b);
+    k_scan_write<<<nsb, kScanBlock, 0, st>>>(b);
     k_scatter<<<b.nblk, kBlock, 0, st>>>(b);
     k_reorder<<<blocks_for((long long)b.C * 32, 256), 256, 0, st>>>(b);
     k_tile_count<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);

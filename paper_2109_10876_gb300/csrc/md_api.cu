@@ -402,6 +402,9 @@ md_status md_create(const md_params *p, md_handle **out)
         R.eps24_u = (float)(24.0 * eps / u);
         R.rl2_lo_u = (float)((rl * rl - brl) / (u * u));
         R.rl2_hi_u = (float)((rl * rl + brl) / (u * u));
+        // beyond this x distance no pair reaches r_list + its band, with room
+        // for the FP32 rounding of tile-relative coordinates (<= 2^8 u per entry)
+        R.rl_win_u = (float)(rl * (1.0 + std::ldexp(1.0, -14)) / u + 2048.0);
         h->reps.push_back(R);
     }
     h->N = h->offsets[nrep];
@@ -480,6 +483,9 @@ md_status md_create(const md_params *p, md_handle **out)
     ok &= (b.cell_count = dalloc<int>(h, h->C)) != nullptr;
     ok &= (b.cell_start = dalloc<int>(h, h->C)) != nullptr;
     ok &= (b.cell_end = dalloc<int>(h, h->C)) != nullptr;
+    int *dpad = dalloc<int>(h, h->C);
+    ok &= dpad != nullptr;
+    ok &= (b.scan_part = dalloc<int>(h, (h->C + mdk::kScanBlock - 1) / mdk::kScanBlock + 1)) != nullptr;
     ok &= (b.bucket = dalloc<int>(h, h->S)) != nullptr;
     ok &= (b.nn = dalloc<int>(h, h->S)) != nullptr;
     ok &= (b.partial = dalloc<double>(h, 4 * (size_t)h->C)) != nullptr;
@@ -503,6 +509,15 @@ md_status md_create(const md_params *p, md_handle **out)
     for (int r = 0; r < nrep; ++r)
         for (int q = 0; q < h->reps[r].ncell[1] * h->reps[r].ncell[2]; ++q) rowrep[h->reps[r].row_off + q] = r;
     ok &= cudaMemcpy(b.row_rep, rowrep.data(), sizeof(int) * h->nrows, cudaMemcpyHostToDevice) == cudaSuccess;
+    // replica slot ranges are padded to kBlock: the padding follows the
+    // replica's last cell in the scan, so the scan yields slot positions directly
+    std::vector<int> pad(h->C, 0);
+    for (int r = 0; r < nrep; ++r)
+        if (h->reps[r].ncells > 0)
+            pad[h->reps[r].cell_off + h->reps[r].ncells - 1] =
+                (int)(round_up(h->reps[r].n, mdk::kBlock) - h->reps[r].n);
+    ok &= cudaMemcpy(dpad, pad.data(), sizeof(int) * h->C, cudaMemcpyHostToDevice) == cudaSuccess;
+    b.cell_pad = dpad;
     ok &= cudaMemcpy(drep, h->reps.data(), sizeof(Replica) * nrep, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemcpy(dblk, blk.data(), sizeof(int) * h->nblk, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemset(b.cell_count, 0, sizeof(int) * h->C) == cudaSuccess;

@@ -33,6 +33,7 @@ namespace mdk {
 constexpr int kBlock = 128;          // threads per block of the per-slot kernels
 constexpr int kMaxReplicas = 4096;
 constexpr int kTileMax = 128;        // particles per tile (one per thread)
+constexpr int kScanBlock = 1024;     // cells per block of the cell scan
 constexpr int kMaxPieces = 18;       // 3 x 3 rows, at most 2 x-pieces each
 
 // error bits latched in Ctl::err
@@ -72,6 +73,7 @@ struct Replica {
     int cubic;                            // all box edges equal: no per-axis scaling
     float ry, rz;                         // L_y / L_x, L_z / L_x
     float rc2_lo_u, rc2_hi_u, fmax2_u, sig2_u, eps24_u, rl2_lo_u, rl2_hi_u;
+    float rl_win_u;                       // x-window half-width of the list walk (> r_list, in u)
 };
 
 // Device control block: every per-step decision lives here, so a step needs
@@ -178,6 +180,8 @@ struct Bufs {
     int *cell_count;         // C
     int *cell_start;         // C
     int *cell_end;           // C (cursor during the scatter, then one past the last slot)
+    const int *cell_pad;     // C: padding slots after a cell (the last cell of each replica)
+    int *scan_part;          // blocks of the cell scan: their sums, then exclusive offsets
     int *row_rep;            // nrows: replica of every row (rows ordered by replica)
     int *bucket;             // S
     unsigned short *nbr;     // K * S halo indices
