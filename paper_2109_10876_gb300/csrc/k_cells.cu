@@ -147,6 +147,52 @@ __global__ void k_get_state(Bufs b, double *xout, double *vout)
 
 __global__ void k_set_rebuild(Ctl *ctl) { ctl->rebuild = 1; }
 
+// New positions (caller order) for the particles in their current slots: the
+// slot order and the Verlet list stay, the fixed-point copies follow, and the
+// largest displacement since the last list build is gathered as after a drift.
+__global__ void __launch_bounds__(kBlock) k_reload(Bufs b, const double *xin)
+{
+    __shared__ float smax[kBlock / 32];
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float ratio = 0.0f;
+    if (s < b.S) {
+        const int cur = b.ctl->cur;
+        const int id = (int)b.pos[cur][s].w;
+        if (id >= 0) {
+            const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
+            unsigned q[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double y = wrap_box(xin[k * b.N + id], R.L[k]);
+                b.x[cur][k * b.S + s] = y;
+                q[k] = to_q(y, R.to_q[k]);
+            }
+            const uint4 p = make_uint4(q[0], q[1], q[2], (unsigned)id);
+            b.pos[cur][s] = p;
+            const uint4 r = b.xref[s];
+            const float dx = (float)(int)(p.x - r.x) * R.qs[0];
+            const float dy = (float)(int)(p.y - r.y) * R.qs[1];
+            const float dz = (float)(int)(p.z - r.z) * R.qs[2];
+            ratio = (dx * dx + dy * dy + dz * dz) / R.disp2_thr;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ratio = fmaxf(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = ratio;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBlock / 32; ++w) ratio = fmaxf(ratio, smax[w]);
+        if (ratio > 0.0f) atomicMax(&b.ctl->disp2_bits, __float_as_uint(ratio));
+    }
+}
+
+// After k_reload: rebuild when some particle moved more than r_skin / 2.
+__global__ void k_reload_decide(Ctl *ctl)
+{
+    const unsigned bits = atomicExch(&ctl->disp2_bits, 0u);
+    ctl->rebuild = (__uint_as_float(bits) > 1.0f) ? 1 : 0;
+}
+
 __global__ void k_cond(Ctl *ctl, cudaGraphConditionalHandle handle, int what)
 {
     const unsigned v = what == 0 ? (ctl->rebuild != 0 && ctl->err == 0) : (ctl->steps_left > 0 && ctl->err == 0);
@@ -890,6 +936,12 @@ void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st)
 }
 
 void launch_set_rebuild(const Bufs &b, cudaStream_t st) { k_set_rebuild<<<1, 1, 0, st>>>(b.ctl); }
+
+void launch_reload(const Bufs &b, const double *x, cudaStream_t st)
+{
+    k_reload<<<b.nblk, kBlock, 0, st>>>(b, x);
+    k_reload_decide<<<1, 1, 0, st>>>(b.ctl);
+}
 
 void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_t st)
 {

@@ -25,7 +25,7 @@ constexpr unsigned kMagicBits = 0x4B400000u;
 constexpr float kFixScale = 4194304.0f;     // 2^22
 constexpr double kFixInv = 1.0 / 4194304.0;
 #ifndef MDK_FORCE_MIN_BLOCKS
-#define MDK_FORCE_MIN_BLOCKS 6
+#define MDK_FORCE_MIN_BLOCKS 4
 #endif
 constexpr int kU = kPad;                     // neighbours per batch: lists are padded to it
 

@@ -46,7 +46,7 @@ struct md_handle {
     double *ad_ck = nullptr;        // checkpoints: (x, v) in caller order, 6 N each
     long long ad_ck_cap = 0;        // checkpoints the buffer holds
     double *ad_fin = nullptr;       // final (x, v), 6 N
-    double *ad_work = nullptr;      // lx, lv, hv, zero v: 4 x 3 N
+    double *ad_work = nullptr;      // lx, lv, hv: 3 x 3 N
     double *ad_seg = nullptr;       // positions of one segment: (k + 1) x 3 N
     long long ad_seg_cap = 0;
     double *ad_small = nullptr;     // coef (4 nrep), g (4 nrep), sums (4 nrep)
@@ -809,13 +809,14 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
 }
 
 // set the handle's state from caller-order device arrays and build its lists
-static md_status adj_load(md_handle *h, const double *x, const double *v, cudaStream_t st)
+// Positions x (caller order, device) into the particles' current slots; the
+// Verlet list is rebuilt only if the displacement since its build asks for it.
+static md_status adj_load(md_handle *h, const double *x, cudaStream_t st)
 {
-    md_status s = md_set_state(h, x, v, st);
-    if (s != MD_OK) return s;
-    mdk::launch_set_rebuild(h->b, st);
+    mdk::launch_reload(h->b, x, st);
     mdk::launch_rebuild_chain(h->b, st);
-    return MD_OK;
+    h->F_valid = false;
+    return cuda_ok(h, cudaGetLastError(), "reload launch") ? MD_OK : MD_ERR_CUDA;
 }
 
 md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, double *dL_dsigma, void *stream)
@@ -826,14 +827,14 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
     const int nrep = h->b.nrep;
     const long long N = h->N, n3 = 3 * N;
     const int T = h->ad_T, k = h->ad_k;
-    if (!h->ad_work && !(h->ad_work = dalloc<double>(h, (size_t)(4 * n3)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    if (!h->ad_work && !(h->ad_work = dalloc<double>(h, (size_t)(3 * n3)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
     if (h->ad_seg_cap < k + 1) {
         h->ad_seg = grow(h, h->ad_seg, (size_t)((k + 1) * n3));
         if (!h->ad_seg) return fail(h, MD_ERR_CUDA, "cannot allocate");
         h->ad_seg_cap = k + 1;
     }
     if (!h->ad_small && !(h->ad_small = dalloc<double>(h, (size_t)(12 * nrep)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
-    double *lx = h->ad_work, *lv = lx + n3, *hv = lv + n3, *vzero = hv + n3;
+    double *lx = h->ad_work, *lv = lx + n3, *hv = lv + n3;
     double *coef = h->ad_small, *g = coef + 4 * nrep, *sums = g + 4 * nrep;
     // loss weights (dL/dU, dL/dK, dL/dW) per replica, from host or device memory
     std::vector<double> in(3 * nrep), cf(12 * nrep, 0.0);
@@ -841,12 +842,11 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
         return MD_ERR_CUDA;
     for (int r = 0; r < nrep; ++r)
         for (int q = 0; q < 3; ++q) cf[4 * r + q] = in[3 * r + q];
-    if (!cuda_ok(h, cudaMemcpyAsync(coef, cf.data(), sizeof(double) * 12 * nrep, cudaMemcpyHostToDevice, st), "upload") ||
-        !cuda_ok(h, cudaMemsetAsync(vzero, 0, sizeof(double) * n3, st), "clear"))
+    if (!cuda_ok(h, cudaMemcpyAsync(coef, cf.data(), sizeof(double) * 12 * nrep, cudaMemcpyHostToDevice, st), "upload"))
         return MD_ERR_CUDA;
     const double half = 0.5 * h->b.dt / h->b.mass;
     // final state: adjoints of the loss and its explicit parameter terms
-    md_status s = adj_load(h, h->ad_fin, h->ad_fin + n3, st);
+    md_status s = adj_load(h, h->ad_fin, st);
     if (s != MD_OK) return s;
     mdk::launch_adj_loss(h->b, coef, lx, lv, sums, st);
     mdk::launch_adj_finish_loss(h->b, sums, coef, g, st);
@@ -866,7 +866,7 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
                 mdk::launch_get_state(h->b, h->ad_seg + (long long)(t - t0) * n3, nullptr, st);
             }
             for (int t = t1; t >= (c == 0 ? 0 : t0 + 1); --t) {
-                s = adj_load(h, h->ad_seg + (long long)(t - t0) * n3, vzero, st);
+                s = adj_load(h, h->ad_seg + (long long)(t - t0) * n3, st);
                 if (s != MD_OK) return s;
                 // the kicks at x_t: the first half kick of step t and the second of step t - 1
                 const double ct = (t == T || t == 0) ? half : 2.0 * half;

@@ -317,6 +317,7 @@ void launch_force(const Bufs &b, int precision, int mode, bool energy, cudaStrea
 void launch_kick_drift(const Bufs &b, cudaStream_t st);
 void launch_get_state(const Bufs &b, double *x, double *v, cudaStream_t st);
 void launch_force_by_id(const Bufs &b, double *buf, int dir, cudaStream_t st);
+void launch_reload(const Bufs &b, const double *x, cudaStream_t st);
 void launch_export_pairs(const Bufs &b, int *pairs, long long cap, unsigned long long *count, cudaStream_t st);
 void launch_set_rebuild(const Bufs &b, cudaStream_t st);
 // graph conditionals: set `handle` to (ctl->rebuild != 0) (what = 0) or (ctl->steps_left > 0) (what = 1)
