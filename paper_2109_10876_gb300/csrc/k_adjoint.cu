@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
         const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
         const double h0 = 0.5 * L0, h1 = 0.5 * L1, h2 = 0.5 * L2;
         const double eps = R.eps, sig = R.sigma, sig2 = sig * sig, rc2 = R.rc2;
+        const double eps24 = 24.0 * eps, isig = 1.0 / sig;
         const double band = 1e-12 * rc2;
         double p0 = 0.0, p1 = 0.0, p2 = 0.0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
@@ -123,10 +124,13 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < rc2 + band)) continue;
                 if (!(r2 < rc2 - band) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < rc2)) continue;
-                const double s2 = sig2 / r2, s6 = s2 * s2 * s2, s12 = s6 * s6;
-                const double g = 24.0 * eps * (2.0 * s12 - s6) / r2;
-                const double gpr = 24.0 * eps * (8.0 * s6 - 28.0 * s12) / (r2 * r2);
-                const double dgds = 24.0 * eps * (24.0 * s12 - 6.0 * s6) / (sig * r2);
+                // one FP64 division per pair (the FP64 divide is a long sequence)
+                const double ir2 = 1.0 / r2;
+                const double s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+                const double e24 = eps24 * ir2;
+                const double g = e24 * (2.0 * s12 - s6);
+                const double gpr = e24 * ir2 * (8.0 * s6 - 28.0 * s12);
+                const double dgds = e24 * isig * (24.0 * s12 - 6.0 * s6);
                 const double d[3] = {dx, dy, dz};
                 if (MODE == 0) {
                     const double dw[3] = {wi[0] - hw[3 * h], wi[1] - hw[3 * h + 1], wi[2] - hw[3 * h + 2]};
@@ -193,6 +197,123 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
     }
 }
 
+// Hessian-vector product for the FP32 + fixed-point forward path (MODE 0 of
+// k_adj in FP32): separations from the fixed-point positions as in the force
+// kernel, the interacting set decided the same way (FP64 within rounding of
+// r_cut), pair terms and per-particle sums in FP32, w staged as FP32 (hi, lo)
+// pairs so that w_i - w_j keeps about 48 bits.  The adjoint state itself
+// (lx, lv) and the parameter projections stay FP64.
+__global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, double *out, double scale, double *acc)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Piece pc[kMaxPieces + 1];
+    __shared__ Tile tl;
+    __shared__ int s_tile, s_np;
+    __shared__ double sm4[kBlock / 32][4];
+    __shared__ bool last;
+    if (b.ctl->err) return;
+    const int cur = b.ctl->cur;
+    const double *X = b.x[cur];
+    const uint4 *P = b.pos[cur];
+    uint4 *hpos = reinterpret_cast<uint4 *>(smem_raw);
+    float4 *hwa = reinterpret_cast<float4 *>(hpos + b.hcap);   // (hi x, hi y, hi z, lo x)
+    float2 *hwb = reinterpret_cast<float2 *>(hwa + b.hcap);    // (lo y, lo z)
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= b.ctl->ntiles) break;
+        load_tile(b, t, tl, pc, s_np);
+        __syncthreads();
+        const Replica &R = b.rep[tl.rep];
+        const int np = s_np;
+        const int Pt = tl.s1 - tl.s0;
+        stage_halo<uint4>(pc, np, [&](int h, int j) {
+            const uint4 q = P[j];
+            hpos[h] = q;
+            const int id = (int)q.w;
+            const double w0 = w[id], w1 = w[b.N + id], w2 = w[2 * b.N + id];
+            const float a0 = (float)w0, a1 = (float)w1, a2 = (float)w2;
+            hwa[h] = make_float4(a0, a1, a2, (float)(w0 - (double)a0));
+            hwb[h] = make_float2((float)(w1 - (double)a1), (float)(w2 - (double)a2));
+        });
+        __syncthreads();
+        const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
+        const float lo = R.rc2_lo, hi = R.rc2_hi;
+        const float eps24 = 24.0f * (float)R.eps, sig2 = (float)(R.sigma * R.sigma), isig = (float)(1.0 / R.sigma);
+        double p0 = 0.0, p1 = 0.0;
+        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+            const uint4 pi = P[i];
+            const int id = (int)pi.w;
+            const int n = min(b.nn[i], b.K);
+            const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
+            const double wi0 = w[id], wi1 = w[b.N + id], wi2 = w[2 * b.N + id];
+            const float ah0 = (float)wi0, ah1 = (float)wi1, ah2 = (float)wi2;
+            const float al0 = (float)(wi0 - (double)ah0), al1 = (float)(wi1 - (double)ah1), al2 = (float)(wi2 - (double)ah2);
+            float acc3[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f}, Fs[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < n; ++k) {
+                const int h = __ldg(nb + (long long)k * Pt);
+                const uint4 pj = hpos[h];
+                const float dx = (float)(int)(pi.x - pj.x) * qs0;
+                const float dy = (float)(int)(pi.y - pj.y) * qs1;
+                const float dz = (float)(int)(pi.z - pj.z) * qs2;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                if (!(r2 < hi)) continue;
+                if (!(r2 < lo) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < R.rc2)) continue;
+                const float ir2 = 1.0f / r2;
+                const float s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+                const float e24 = eps24 * ir2;
+                const float g = e24 * (2.0f * s12 - s6);
+                const float gpr = e24 * ir2 * (8.0f * s6 - 28.0f * s12);
+                const float dgds = e24 * isig * (24.0f * s12 - 6.0f * s6);
+                const float4 wa = hwa[h];
+                const float2 wb = hwb[h];
+                const float dw0 = (ah0 - wa.x) + (al0 - wa.w);
+                const float dw1 = (ah1 - wa.y) + (al1 - wb.x);
+                const float dw2 = (ah2 - wa.z) + (al2 - wb.y);
+                const float ddw = dx * dw0 + dy * dw1 + dz * dw2;
+                const float gd = gpr * ddw;
+                acc3[0] += g * dw0 + gd * dx;
+                acc3[1] += g * dw1 + gd * dy;
+                acc3[2] += g * dw2 + gd * dz;
+                F[0] += g * dx; F[1] += g * dy; F[2] += g * dz;
+                Fs[0] += dgds * dx; Fs[1] += dgds * dy; Fs[2] += dgds * dz;
+            }
+            for (int q = 0; q < 3; ++q) out[q * b.N + id] = (double)acc3[q];
+            p0 += (wi0 * F[0] + wi1 * F[1] + wi2 * F[2]) / R.eps;
+            p1 += wi0 * Fs[0] + wi1 * Fs[1] + wi2 * Fs[2];
+        }
+        // per-tile partials in a fixed order
+        for (int o = 16; o > 0; o >>= 1) {
+            p0 += __shfl_down_sync(0xffffffffu, p0, o);
+            p1 += __shfl_down_sync(0xffffffffu, p1, o);
+        }
+        if ((threadIdx.x & 31) == 0) { sm4[threadIdx.x >> 5][0] = p0; sm4[threadIdx.x >> 5][1] = p1; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, c = 0;
+            for (int q = 0; q < kBlock / 32; ++q) { a += sm4[q][0]; c += sm4[q][1]; }
+            b.partial[4 * t + 0] = a;
+            b.partial[4 * t + 1] = c;
+            b.partial[4 * t + 2] = 0.0;
+            b.partial[4 * t + 3] = 0.0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&b.ctl->done_force, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    adj_reduce(b, scale, acc);
+    if (threadIdx.x == 0) {
+        b.ctl->tile_next = 0u;
+        b.ctl->done_force = 0u;
+    }
+}
+
 // lx += c hv; then lv += dt lx (caller order, 3 N values each).
 __global__ void k_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt)
 {
@@ -227,8 +348,18 @@ static int adj_grid(const void *fn, size_t smem)
 }
 
 // hv = J w at the current state; g[4 r + k] += scale * (w.F/eps, w.dF/dsigma)_r.
-void launch_adj_hvp(const Bufs &b, const double *w, double *hv, double scale, double *g, cudaStream_t st)
+// precision 1: FP32 pair terms (k_adj_hvp32), else FP64.
+void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, double scale, double *g,
+                    cudaStream_t st)
 {
+    if (precision == 1) {
+        const size_t smem32 = (size_t)b.hcap * (sizeof(uint4) + sizeof(float4) + sizeof(float2));
+        static int grid32 = 0;
+        static size_t gs32 = 0;
+        if (grid32 == 0 || gs32 != smem32) { grid32 = adj_grid((const void *)k_adj_hvp32, smem32); gs32 = smem32; }
+        k_adj_hvp32<<<grid32, kBlock, smem32, st>>>(b, w, hv, scale, g);
+        return;
+    }
     const size_t smem = (size_t)b.hcap * 6 * sizeof(double);
     static int grid = 0;
     static size_t gs = 0;

@@ -870,7 +870,7 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
                 if (s != MD_OK) return s;
                 // the kicks at x_t: the first half kick of step t and the second of step t - 1
                 const double ct = (t == T || t == 0) ? half : 2.0 * half;
-                mdk::launch_adj_hvp(h->b, lv, hv, ct, g, st);
+                mdk::launch_adj_hvp(h->b, h->precision, lv, hv, ct, g, st);
                 mdk::launch_adj_update(n3, lx, lv, hv, ct, t > 0 ? h->b.dt : 0.0, st);
             }
         }

@@ -323,7 +323,8 @@ void launch_set_rebuild(const Bufs &b, cudaStream_t st);
 // graph conditionals: set `handle` to (ctl->rebuild != 0) (what = 0) or (ctl->steps_left > 0) (what = 1)
 void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_t st);
 void launch_set_steps(const Bufs &b, long long left, cudaStream_t st);
-void launch_adj_hvp(const Bufs &b, const double *w, double *hv, double scale, double *g, cudaStream_t st);
+void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, double scale, double *g,
+                    cudaStream_t st);
 void launch_adj_loss(const Bufs &b, const double *coef, double *lx, double *lv, double *sums, cudaStream_t st);
 void launch_adj_finish_loss(const Bufs &b, const double *sums, const double *coef, double *g, cudaStream_t st);
 void launch_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt, cudaStream_t st);

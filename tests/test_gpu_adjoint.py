@@ -33,12 +33,14 @@ def loss_coefs(n, box):
     return np.array([1.0 / n, 2.0 / (3 * V), 1.0 / (3 * V)])
 
 
-@pytest.mark.parametrize("precision,T,k,tol", [(0, 30, 10, 1e-8), (0, 7, 3, 1e-8), (1, 30, 10, 1e-3)])
+@pytest.mark.parametrize("precision,T,k,tol", [(0, 30, 10, 1e-8), (0, 7, 3, 1e-8), (1, 7, 3, 2e-4),
+                                                (1, 30, 10, 1e-3)])
 def test_backward_matches_oracle_adjoint(md, precision, T, k, tol):
     """d(U/N + (2K + W)/(3V))/d(eps, sigma) per replica after T steps: the GPU
     reverse pass (checkpoints every k steps) equals the oracle's reverse pass.
     With an FP32 forward the trajectory itself differs from the FP64 one at
-    the 1e-6 level, so the agreement is looser."""
+    the 1e-6 level and the Hessian-vector products use FP32 pair terms, so the
+    agreement is looser."""
     reps = two_replicas()
     sizes = [len(r[0]) for r in reps]
     boxes = np.array([r[2] for r in reps])
