@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ncell", type=int, default=NCELL)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64, CPU baseline and force error")
-    ap.add_argument("--workload", default="lj", choices=["lj", "melt", "slab"],
-                    help="lj: the LJ fluid line (default); melt / slab: one line for that workload")
+    ap.add_argument("--workload", default="lj", choices=["lj", "melt", "slab", "sphere"],
+                    help="lj: the LJ fluid line (default); melt / slab / sphere: one line for that workload")
     return ap.parse_args()
 
 
@@ -335,6 +335,28 @@ def run_slab(md, torch, dev, args):
     h.destroy()
 
 
+def run_sphere(md, torch, dev, args):
+    """Spherical inhomogeneous LJ system (the paper's load-imbalance case):
+    2.58 million particles at density 0.8442 in a central sphere of a cubic box
+    of edge 271, vacuum around it, Langevin thermostat at T = 0.1 (gamma 0.5),
+    rc 2.5, skin 0.3, dt 0.005."""
+    from paper_2109_10876_gb300 import inputs
+    t0 = time.perf_counter()
+    x, v, box = inputs.sphere()
+    n = len(x)
+    h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED,
+                     langevin_gamma=0.5, kT=0.1, seed=6)
+    md.md_set_state(h, torch.tensor(x.T.copy(), device=dev), torch.tensor(v.T.copy(), device=dev))
+    md.md_build_neighbors(h)
+    md.md_autotune(h, 10)
+    prep = f"fcc sites nearest the centre: {time.perf_counter() - t0:.1f} s"
+    workload_line(md, torch, dev, args, "LJ sphere in vacuum", n, h, prep,
+                  {"workload": f"LJ sphere, N = {n} at rho 0.8442 (radius 90.0) in a cubic box of edge 271, "
+                               f"Langevin T 0.1 (gamma 0.5), rc 2.5, skin 0.3, dt 0.005",
+                   "l2": "working set about 800 MB (larger than L2)"})
+    h.destroy()
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -389,6 +411,9 @@ def main():
         return
     if args.workload == "slab":
         run_slab(md, torch, dev, args)
+        return
+    if args.workload == "sphere":
+        run_sphere(md, torch, dev, args)
         return
     x, v, box = inputs.lj_fluid(args.ncell, rho=RHO, T=T0, seed=2 + rank)
     n = len(x)

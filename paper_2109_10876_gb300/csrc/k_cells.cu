@@ -616,29 +616,96 @@ template <> struct Cand<false> {
     __device__ static int index(const uint4 &, int h) { return h; }
 };
 
-// Verlet lists of one tile (Sec. 2.1.2): each warp takes 32 consecutive
-// particles and walks the union of their 27-cell stencils, candidate by
-// candidate (a shared-memory broadcast), keeping j when |d_ij| < r_cut + r_skin.
-// Candidates whose FP32 r^2 lies within rounding of the list radius are
-// decided in FP64 from the master positions (one vote per batch of 4).
-// Appends are branch-free: every candidate is written at the lane's next free
-// row and the row pointer advances only on a hit.  The shared stage has the
-// final [row][particle] layout of the tile's list block; a list that outgrows
-// it is walked again straight into global memory (rare).
+// Halo range `lane` (< 2 nrow) of the union of the stencils of particles
+// [g0, g1] of the tile (cells [xa - 1, xb + 1] on each of the nrow halo rows,
+// split at the periodic boundary), trimmed for REL to the x-window of the
+// first and last of those particles.  Returns (h0, h1, j0): halo indices
+// [h0, h1) with first slot j0; empty for other lanes or an empty group.
 template <bool REL>
-__device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
-                                              const typename Cand<REL>::T *halo, unsigned short *lst, const double *X,
-                                              int hfirst, int *s_kmax, int &mx, long long &sm, int &err)
+__device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
+                                            const typename Cand<REL>::T *halo, int hfirst, int g0, int g1, int lane,
+                                            int &rh0, int &rh1, int &rj0, int &err)
 {
-    using C = Cand<REL>;
-    using T = typename C::T;
-    const float ry = R.ry, rz = R.rz;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
     int ly, cntY, lz, cntZ;
     axis_offsets(ny, ly, cntY);
     axis_offsets(nz, lz, cntZ);
     const int nrow = cntY * cntZ;
+    rh0 = rh1 = rj0 = 0;
+    if (g0 > g1 || lane >= nrow * 2) return;
+    const int xa = (b.cellid[tl.s0 + g0] - R.cell_off) % nx;
+    const int xb = (b.cellid[tl.s0 + g1] - R.cell_off) % nx;
+    const bool whole = xb - xa + 3 >= nx;
+    const int row = lane >> 1, part = lane & 1;
+    const int oz = row / cntY, oy = row - oz * cntY;
+    const int zz = wrapi(tl.cz + lz + oz, nz), yy = wrapi(tl.cy + ly + oy, ny);
+    const int base = R.cell_off + (zz * ny + yy) * nx;
+    int ca = -1, cb = -1;     // cells [ca, cb) of this part
+    if (whole) { if (part == 0) { ca = 0; cb = nx; } }
+    else {
+        const int a = xa - 1, e = xb + 2;    // [a, e) before wrapping
+        if (a < 0) { if (part == 0) { ca = a + nx; cb = nx; } else { ca = 0; cb = e; } }
+        else if (e > nx) { if (part == 0) { ca = a; cb = nx; } else { ca = 0; cb = e - nx; } }
+        else if (part == 0) { ca = a; cb = e; }
+    }
+    if (!(ca >= 0 && cb > ca)) return;
+    int qq = 0;
+    while (qq + 1 < np && !(pc[qq].row == row && pc[qq].xa <= ca && ca < pc[qq].xb)) ++qq;
+    const int j0 = b.cell_start[base + ca], j1 = b.cell_end[base + cb - 1];
+    rh0 = pc[qq].hoff + (j0 - pc[qq].slot0);
+    rh1 = rh0 + (j1 - j0);
+    rj0 = j0;
+    if (rh0 < pc[qq].hoff || rh1 > pc[qq].hoff + pc[qq].n) { err |= kErrList; rh1 = rh0; return; }
+    if constexpr (REL) {
+        // Rows are sorted along x (cells in order, members by x), and so are
+        // the group's own particles: candidates farther along x than the
+        // window from the first and last of them are out of reach of all.
+        const float xlo = halo[hfirst + g0].x - R.rl_win_u;
+        const float xhi = halo[hfirst + g1].x + R.rl_win_u;
+        int a = rh0, e = rh1;
+        while (a < e) {
+            const int m = (a + e) >> 1;
+            if (halo[m].x < xlo) a = m + 1; else e = m;
+        }
+        int a2 = a;
+        e = rh1;
+        while (a2 < e) {
+            const int m = (a2 + e) >> 1;
+            if (halo[m].x <= xhi) a2 = m + 1; else e = m;
+        }
+        rj0 += a - rh0;
+        rh0 = a;
+        rh1 = a2;
+    }
+}
+
+// Verlet lists of one tile (Sec. 2.1.2).  Each half-warp takes 16
+// consecutive particles and walks the union of their 27-cell stencils,
+// candidate by candidate (a shared-memory broadcast per half), keeping j when
+// |d_ij| < r_cut + r_skin.  The ranges of both unions sit in the warp's table
+// `rng` ([half][range][h0, h1, j0]), so no loop below needs the other lanes:
+// the two halves run their own ranges side by side.  Candidates whose FP32
+// r^2 lies within rounding of the list radius are set aside and decided
+// afterwards in FP64 from the master positions (rare), appended after the
+// others.  Appends are branch-free: every candidate is written at the lane's
+// next free row and the row pointer advances only on a hit.  The shared stage
+// has the final [row][particle] layout of the tile's list block; a list that
+// outgrows it is walked again straight into global memory (rare).
+template <bool REL>
+__device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
+                                              const typename Cand<REL>::T *halo, unsigned short *lst, const double *X,
+                                              int hfirst, int (*rng)[kMaxPieces][3], int *s_kmax, int &mx,
+                                              long long &sm, int &err)
+{
+    using C = Cand<REL>;
+    using T = typename C::T;
+    const float ry = R.ry, rz = R.rz;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int half = lane >> 4;
+    int ly, cntY, lz, cntZ;
+    axis_offsets(R.ncell[1], ly, cntY);
+    axis_offsets(R.ncell[2], lz, cntZ);
+    const int nrng = 2 * cntY * cntZ;
     const float lo = R.rl2_lo_u, hi = R.rl2_hi_u;
     const int Pt = tl.s1 - tl.s0;
     // stage rows of this tile (0: no stage, every list goes to global memory)
@@ -648,60 +715,14 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         const int pp = c0 + lane;
         const bool valid = pp < Pt;
         const int i = tl.s0 + (valid ? pp : c0);
-        const int xa = (b.cellid[tl.s0 + c0] - R.cell_off) % nx;
-        const int xb = (b.cellid[tl.s0 + min(c0 + 31, Pt - 1)] - R.cell_off) % nx;
-        // union x-range of cells: [xa - 1, xb + 1], or the whole row
-        const int span = xb - xa + 3;
-        const bool whole = span >= nx;
-        // lane r (< nrow * 2) holds halo range r of the union
-        int rh0 = 0, rh1 = 0, rj0 = 0;
-        if (lane < nrow * 2) {
-            const int row = lane >> 1, part = lane & 1;
-            const int oz = row / cntY, oy = row - oz * cntY;
-            const int zz = wrapi(tl.cz + lz + oz, nz), yy = wrapi(tl.cy + ly + oy, ny);
-            const int base = R.cell_off + (zz * ny + yy) * nx;
-            int ca = -1, cb = -1;     // cells [ca, cb) of this part
-            if (whole) { if (part == 0) { ca = 0; cb = nx; } }
-            else {
-                const int a = xa - 1, e = xb + 2;    // [a, e) before wrapping
-                if (a < 0) { if (part == 0) { ca = a + nx; cb = nx; } else { ca = 0; cb = e; } }
-                else if (e > nx) { if (part == 0) { ca = a; cb = nx; } else { ca = 0; cb = e - nx; } }
-                else if (part == 0) { ca = a; cb = e; }
-            }
-            if (ca >= 0 && cb > ca) {
-                int qq = 0;
-                while (qq + 1 < np && !(pc[qq].row == row && pc[qq].xa <= ca && ca < pc[qq].xb)) ++qq;
-                const int j0 = b.cell_start[base + ca], j1 = b.cell_end[base + cb - 1];
-                rh0 = pc[qq].hoff + (j0 - pc[qq].slot0);
-                rh1 = rh0 + (j1 - j0);
-                rj0 = j0;
-                if (rh0 < pc[qq].hoff || rh1 > pc[qq].hoff + pc[qq].n) { err |= kErrList; rh1 = rh0; }
-            }
+        {
+            int h0, h1, j0;
+            union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0, err);
+            if (lane < nrng) { rng[0][lane][0] = h0; rng[0][lane][1] = h1; rng[0][lane][2] = j0; }
+            union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0, err);
+            if (lane < nrng) { rng[1][lane][0] = h0; rng[1][lane][1] = h1; rng[1][lane][2] = j0; }
         }
-        if constexpr (REL) {
-            // Rows are sorted along x (cells in order, members by x), and so
-            // are the warp's own particles: candidates farther along x than
-            // the window from the first and last of them are out of reach of
-            // all 32.  Each range is trimmed by two binary searches.
-            const float xlo = halo[hfirst + c0].x - R.rl_win_u;
-            const float xhi = halo[hfirst + min(c0 + 31, Pt - 1)].x + R.rl_win_u;
-            if (rh1 > rh0) {
-                int a = rh0, e = rh1;
-                while (a < e) {
-                    const int m = (a + e) >> 1;
-                    if (halo[m].x < xlo) a = m + 1; else e = m;
-                }
-                int a2 = a;
-                e = rh1;
-                while (a2 < e) {
-                    const int m = (a2 + e) >> 1;
-                    if (halo[m].x <= xhi) a2 = m + 1; else e = m;
-                }
-                rj0 += a - rh0;
-                rh0 = a;
-                rh1 = a2;
-            }
-        }
+        __syncwarp();
         const int self = valid ? hfirst + pp : -1;
         const T p = halo[hfirst + (valid ? pp : c0)];
         // this lane's stage column (row stride Pt); lanes without one write a
@@ -710,70 +731,71 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         unsigned short *col = own ? lst + pp : dummy + lane;
         const int stride = own ? Pt : 0;
         int cnt = 0;
-        for (int r = 0; r < nrow * 2; ++r) {
-            const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
-            const int j0 = __shfl_sync(0xffffffffu, rj0, r);
-            int h = h0;
+        bool tie = false;
+        for (int r = 0; r < nrng; ++r) {
+            const int h1 = rng[half][r][1];
+            int h = rng[half][r][0];
             for (; h + 4 <= h1; h += 4) {
                 T pj[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) pj[u] = halo[h + u];
-                float r2[4];
-                bool in[4];
-                bool bnd = false;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    r2[u] = C::sep2(p, pj[u], ry, rz);
-                    in[u] = (r2[u] < lo) & (C::index(pj[u], h + u) != self);
-                    bnd |= (r2[u] < hi) & !(r2[u] < lo);
-                }
-                if (__any_sync(0xffffffffu, bnd)) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (valid & (r2[u] < hi) & !(r2[u] < lo) & (h + u != self))
-                            in[u] = r2_fp64(X, b.S, i, j0 + (h + u - h0), R.L) < R.rl2;
-                }
                 // four free rows from here while cnt <= cap - 4 (else re-walked below)
                 unsigned short *q = col + max(min(cnt, cap - 4), 0) * stride;
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
+                    const float r2 = C::sep2(p, pj[u], ry, rz);
+                    const bool in = (r2 < lo) & (C::index(pj[u], h + u) != self);
+                    tie |= (r2 < hi) & !(r2 < lo);
                     *q = (unsigned short)C::index(pj[u], h + u);
-                    q += in[u] ? stride : 0;
-                    cnt += in[u];
+                    q += in ? stride : 0;
+                    cnt += in;
                 }
             }
             for (; h < h1; ++h) {
                 const float r2 = C::sep2(p, halo[h], ry, rz);
-                const bool mine = valid & (h != self);
-                bool in = (r2 < lo) & mine;
-                const bool band = (r2 < hi) & !(r2 < lo) & mine;
-                if (__any_sync(0xffffffffu, band) && band)
-                    in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
+                const bool in = (r2 < lo) & (h != self);
+                tie |= (r2 < hi) & !(r2 < lo);
                 col[max(min(cnt, cap - 4), 0) * stride] = (unsigned short)h;
                 cnt += in;
             }
         }
-        // a list longer than the stage allows (or a tile without a stage):
-        // walk the candidates again; rows below cap go to the stage, the rest
-        // to global memory
-    const bool over = valid && (cnt > cap - 4);
-        if (__any_sync(0xffffffffu, over)) {
-            int c2 = 0;
-            for (int r = 0; r < nrow * 2; ++r) {
-                const int h0 = __shfl_sync(0xffffffffu, rh0, r), h1 = __shfl_sync(0xffffffffu, rh1, r);
-                const int j0 = __shfl_sync(0xffffffffu, rj0, r);
+        // candidates within rounding of the list radius: FP64, appended
+        if (tie && valid) {
+            for (int r = 0; r < nrng; ++r) {
+                const int h0 = rng[half][r][0], h1 = rng[half][r][1], j0 = rng[half][r][2];
                 for (int h = h0; h < h1; ++h) {
                     const float r2 = C::sep2(p, halo[h], ry, rz);
-                    const bool mine = valid & (h != self);
-                    bool in = (r2 < lo) & mine;
-                    if ((r2 < hi) & !(r2 < lo) & mine) in = r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2;
-                    if (in && over) {
-                        if (c2 < cap) lst[c2 * Pt + pp] = (unsigned short)h;
-                        else if (c2 < b.K) b.nbr[nbr_index(tl.s0, Pt, b.K, c2, pp)] = (unsigned short)h;
+                    if ((r2 < hi) & !(r2 < lo) & (h != self) && r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2) {
+                        col[max(min(cnt, cap - 1), 0) * stride] = (unsigned short)h;
+                        ++cnt;
                     }
-                    c2 += in;
                 }
             }
+        }
+        // a list longer than the stage allows (or a tile without a stage):
+        // walk the candidates again in the same order; rows below cap go to
+        // the stage, the rest to global memory
+        if (valid && cnt > cap - 4) {
+            int c2 = 0;
+            auto put = [&](int h) {
+                if (c2 < cap) lst[c2 * Pt + pp] = (unsigned short)h;
+                else if (c2 < b.K) b.nbr[nbr_index(tl.s0, Pt, b.K, c2, pp)] = (unsigned short)h;
+                ++c2;
+            };
+            for (int r = 0; r < nrng; ++r)
+                for (int h = rng[half][r][0]; h < rng[half][r][1]; ++h) {
+                    const float r2 = C::sep2(p, halo[h], ry, rz);
+                    if ((r2 < lo) & (h != self)) put(h);
+                }
+            if (tie)
+                for (int r = 0; r < nrng; ++r) {
+                    const int h0 = rng[half][r][0], h1 = rng[half][r][1], j0 = rng[half][r][2];
+                    for (int h = h0; h < h1; ++h) {
+                        const float r2 = C::sep2(p, halo[h], ry, rz);
+                        if ((r2 < hi) & !(r2 < lo) & (h != self) && r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2)
+                            put(h);
+                    }
+                }
         }
         if (valid) {
             // pad with the particle's own index (r = 0 is never an interaction)
@@ -788,6 +810,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             mx = max(mx, cnt);
             sm += cnt;
         }
+        __syncwarp();   // the range table is rewritten for the next group
     }
 }
 
@@ -800,6 +823,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
     __shared__ Piece pc[kMaxPieces + 1];
     __shared__ Tile tl;
     __shared__ int s_tile, s_np, s_kmax;
+    __shared__ int s_rng[kBlock / 32][2][kMaxPieces][3];   // per warp: the ranges of both half-warp unions
     const int src = b.ctl->cur ^ 1;          // k_reorder wrote the sorted state here
     const uint4 *P = b.pos[src];
     const double *X = b.x[src];
@@ -846,8 +870,8 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
         }
         __syncthreads();
         const int hfirst = tile_self_offset(R, tl, pc, s_np);
-        if (rel) cells_of_tile<true>(b, R, tl, pc, s_np, halof, lst, X, hfirst, &s_kmax, mx, sm, err);
-        else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, &s_kmax, mx, sm, err);
+        if (rel) cells_of_tile<true>(b, R, tl, pc, s_np, halof, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
+        else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
         __syncthreads();
         if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;
         // the staged rows are the start of the tile's list block: one

@@ -301,3 +301,24 @@ def melt(nchain=2000, nbead=200, rho=0.85, T=1.0, seed=4, bond=0.97):
     bonds = np.stack([first, first + 1], axis=1).astype(np.int32)
     v = maxwell_velocities(n, T, seed + 31)
     return x, v, box, bonds
+
+
+def sphere(n=2_580_000, L=271.0, rho=0.8442, T=0.1, seed=6):
+    """Spherical inhomogeneous LJ system (Sec. 4.2): a cubic box of edge L
+    with n particles at density rho in a central sphere and vacuum around it.
+    The particles are the n fcc sites (lattice constant (4/rho)^(1/3), one
+    site at the box centre) closest to the centre, so the sphere radius is
+    about (3 n / (4 pi rho))^(1/3); Gaussian velocities at T."""
+    a = (4.0 / rho) ** (1.0 / 3.0)
+    R = (3.0 * n / (4.0 * math.pi * rho)) ** (1.0 / 3.0)
+    k = int(math.ceil((R + 2 * a) / a))
+    g = np.arange(-k, k, dtype=np.float64)
+    cz, cy, cx = np.meshgrid(g, g, g, indexing="ij")
+    cells = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1)
+    sites = (cells[:, None, :] + FCC_BASIS[None, :, :]).reshape(-1, 3) * a
+    r2 = np.einsum("ij,ij->i", sites, sites)
+    order = np.argsort(r2, kind="stable")[:n]
+    box = np.array([L, L, L])
+    x = wrap(sites[np.sort(order)] + 0.5 * L, box)
+    v = maxwell_velocities(n, T, seed)
+    return x, v, box
