@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
     __shared__ int s_tile, s_np;
     __shared__ double sm4[kBlock / 32][4];
     __shared__ bool last;
-    if (b.ctl->err) return;
+    if (block_uniform(b.ctl->err != 0)) return;
     const int cur = b.ctl->cur;
     const double *X = b.x[cur];
     const uint4 *P = b.pos[cur];
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
     __shared__ int s_tile, s_np;
     __shared__ double sm4[kBlock / 32][4];
     __shared__ bool last;
-    if (b.ctl->err) return;
+    if (block_uniform(b.ctl->err != 0)) return;
     const int cur = b.ctl->cur;
     const double *X = b.x[cur];
     const uint4 *P = b.pos[cur];

@@ -260,7 +260,7 @@ __device__ int block_excl_scan(int v, int *warp_sums, int &total)
 // after its last cell, so the result is the first slot of every cell.
 __global__ void __launch_bounds__(kScanBlock) k_scan_sum(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
+    if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     __shared__ int warp_sums[33];
     const int c = blockIdx.x * kScanBlock + threadIdx.x;
     const int k = c < b.C ? b.cell_count[c] : 0;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sum(Bufs b)
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_top(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
+    if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     __shared__ int warp_sums[33];
     const int nb = (b.C + kScanBlock - 1) / kScanBlock;
     int carry = 0;
@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(Bufs b)
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_write(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
+    if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     __shared__ int warp_sums[33];
     const int c = blockIdx.x * kScanBlock + threadIdx.x;
     const int v = c < b.C ? b.cell_count[c] + b.cell_pad[c] : 0;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_tile_count(Bufs b)
 // Exclusive scan of tiles per row (one block); first tile of every replica.
 __global__ void __launch_bounds__(kScanThreads) k_tile_scan(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
+    if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     __shared__ int warp_sums[33];
     const int n = b.nrows;
     const int chunk = (n + kScanThreads - 1) / kScanThreads;
@@ -816,7 +816,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
 
 __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
+    if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     extern __shared__ uint4 halo[];
     float4 *halof = reinterpret_cast<float4 *>(halo);                          // the same entries, converted
     unsigned short *lst = reinterpret_cast<unsigned short *>(halo + b.hcap);   // [k][Pt] stage, then 32 dummy slots

@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     __shared__ int s_nn[kTileMax];
     __shared__ double sm3[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
-    if (b.ctl->err) return;
+    if (block_uniform(b.ctl->err != 0)) return;
     const int cur = b.ctl->cur, nxt = cur ^ 1;
     const long long step = b.ctl->step;
     const double *X = b.x[cur];
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
 __global__ void __launch_bounds__(kBlock) k_kick_drift(Bufs b)
 {
     __shared__ float smr[kBlock / 32];
-    if (b.ctl->err) return;
+    if (block_uniform(b.ctl->err != 0)) return;
     const int cur = b.ctl->cur, nxt = cur ^ 1;
     const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
     const Replica &R = b.rep[b.blk_rep[blockIdx.x]];

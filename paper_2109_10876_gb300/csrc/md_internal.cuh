@@ -104,7 +104,7 @@ struct Tile {
     int kmax;   // longest padded list of the tile (written by the list build)
 };
 
-constexpr int kListStage = 104;      // list rows of a full tile staged in shared memory (x kTileMax entries)
+constexpr int kListStage = 96;       // list rows of a full tile staged in shared memory (x kTileMax entries)
 
 // One contiguous slot range of a halo: cells [xa, xb) of halo row `row`,
 // placed at halo offset hoff.
@@ -240,6 +240,11 @@ __device__ __forceinline__ void prefetch_l1(const void *gmem)
     asm volatile("prefetch.global.L1 [%0];" ::"l"(gmem));
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *gmem)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(gmem));
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -253,6 +258,19 @@ __device__ __forceinline__ void load_tile(const Bufs &b, int t, Tile &tl, Piece 
     int *dst = reinterpret_cast<int *>(pc);
     constexpr int words = (kMaxPieces + 1) * sizeof(Piece) / sizeof(int);
     for (int m = threadIdx.x; m < words; m += blockDim.x) dst[m] = src[m];
+}
+
+// A decision taken by thread 0 and shared with the whole block, so that every
+// thread of a block takes the same early return: an error latched by another
+// block while this one starts cannot split it across its barriers.
+__device__ __forceinline__ bool block_uniform(bool v)
+{
+    __shared__ int s_flag;
+    if (threadIdx.x == 0) s_flag = v ? 1 : 0;
+    __syncthreads();
+    const bool r = s_flag != 0;
+    __syncthreads();                    // before any later use of s_flag
+    return r;
 }
 
 // Halo index of the tile's first particle.  The tile's own cells lie,
