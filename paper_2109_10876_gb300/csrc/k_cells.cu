@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
     const int src = b.ctl->cur ^ 1;          // k_reorder wrote the sorted state here
     const uint4 *P = b.pos[src];
     const double *X = b.x[src];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5;
     int mx = 0;
     long long sm = 0;
     int err = 0;
