@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--ncell", type=int, default=NCELL)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64, CPU baseline and force error")
-    ap.add_argument("--workload", default="lj", choices=["lj", "melt", "slab", "sphere"],
-                    help="lj: the LJ fluid line (default); melt / slab / sphere: one line for that workload")
+    ap.add_argument("--workload", default="lj", choices=["lj", "melt", "rings", "slab", "sphere"],
+                    help="lj: the LJ fluid line (default); melt / rings / slab / sphere: one line for that workload")
     return ap.parse_args()
 
 
@@ -314,6 +314,50 @@ def run_melt(md, torch, dev, args):
     h.destroy()
 
 
+def run_rings(md, torch, dev, args):
+    """The paper's own polymer melt: 1600 ring polymers of 200 beads (N =
+    320,000) at bead density 0.85, WCA (r_cut = 2^(1/6)) on all pairs, FENE
+    (K 30, R0 1.5), the cosine angle term (K 1.5), Langevin gamma 0.5 at T 1,
+    dt 0.005, skin 0.4.  Preparation (untimed): closed random walks, the
+    cosine push-off with A ramped 1 -> 100 (FP64, bonds and angles on), then
+    300 WCA steps."""
+    from paper_2109_10876_gb300 import inputs
+    t0 = time.perf_counter()
+    x, v, box, bonds, angles = inputs.rings(1600, 200, rho=0.85, T=1.0, seed=7)
+    n = len(x)
+    xt = torch.tensor(x.T.copy(), device=dev)
+    vt = torch.tensor(v.T.copy(), device=dev)
+    rc = 2 ** (1 / 6)
+    common = dict(skin=0.4, bonds=bonds, fene_K=30.0, fene_R0=1.5, angles=angles, angle_K=1.5,
+                  langevin_gamma=0.5, kT=1.0)
+    for k, A in enumerate((1.0, 2.0, 5.0, 10.0, 20.0, 50.0, 100.0)):
+        hp = md.md_create(n, box, potential=md.MD_SOFT, rc_over_sigma=rc, eps=A, dt=0.005,
+                          precision=md.MD_FP64, seed=300 + k, **common)
+        md.md_set_state(hp, xt, vt)
+        md.md_build_neighbors(hp)
+        md.md_step(hp, 300)
+        md.md_get_state(hp, xt, vt)
+        hp.destroy()
+    hw = md.md_create(n, box, potential=md.MD_WCA, dt=0.005, precision=md.MD_FP32_FIXED, seed=400, **common)
+    md.md_set_state(hw, xt, vt)
+    md.md_build_neighbors(hw)
+    md.md_step(hw, 300)
+    md.md_get_state(hw, xt, vt)
+    hw.destroy()
+    h = md.md_create(n, box, potential=md.MD_WCA, dt=0.005, precision=md.MD_FP32_FIXED, seed=7, **common)
+    md.md_set_state(h, xt, vt)
+    md.md_build_neighbors(h)
+    md.md_autotune(h, 10)
+    prep = f"closed random walks, cosine push-off A = 1..100 (7 x 300 FP64 steps), 300 WCA steps: " \
+           f"{time.perf_counter() - t0:.1f} s"
+    workload_line(md, torch, dev, args, "ring polymer melt", n, h, prep,
+                  {"workload": f"ring polymer melt, 1600 x 200 (N = {n}), bead density 0.85, WCA + FENE "
+                               f"(K 30, R0 1.5) + cosine angle (K 1.5) + Langevin (gamma 0.5, T 1), dt 0.005, "
+                               f"skin 0.4",
+                   "l2": "working set about 50 MB (below L2); the timed steps run back to back"})
+    h.destroy()
+
+
 def run_slab(md, torch, dev, args):
     """Liquid/vapour slab: 1,000,000 LJ particles, Lz = 4 Lx = 4 Ly, liquid at
     0.80 in the central quarter of z, vapour at 0.02 elsewhere, random
@@ -408,6 +452,9 @@ def main():
     stream = torch.cuda.current_stream()
     if args.workload == "melt":
         run_melt(md, torch, dev, args)
+        return
+    if args.workload == "rings":
+        run_rings(md, torch, dev, args)
         return
     if args.workload == "slab":
         run_slab(md, torch, dev, args)

@@ -87,6 +87,14 @@ typedef struct {
     const int32_t *bonds;           /* 2 * n_bonds particle indices, or NULL    */
     int32_t list_capacity;          /* neighbours per particle; 0 = automatic   */
     int32_t reserved0;
+    double angle_K;                 /* bending constant of the angle term       */
+    int64_t n_angles;               /* angle triples                            */
+    const int32_t *angles;          /* 3 * n_angles particle indices (a, b, c),
+                                       b the middle bead, or NULL: the cosine
+                                       term K (1 - cos theta) on the angle
+                                       between b1 = x_b - x_a and b2 = x_c - x_b
+                                       (Sec. 4 names a cosine-type term on
+                                       triples without its form)                */
 } md_params;
 
 /* Counters and diagnostics (md_get_stats). */
@@ -133,11 +141,12 @@ md_status md_get_state(md_handle *h, double *x, double *v, void *stream);
 md_status md_build_neighbors(md_handle *h, void *stream);
 
 /* Evaluate the conservative forces (pair potential of Eq. 2 under r < r_cut,
- * plus FENE bonds) at the current positions.  f_out (may be NULL) receives the
+ * plus FENE bonds and angle triples) at the current positions.  f_out (may be NULL) receives the
  * (3, N) FP64 forces in the caller's order; euw_out (may be NULL) receives
  * (U, K, W) per replica, 3 * n_replicas FP64: potential energy (pair energy
- * shifted to 0 at r_cut, plus FENE), kinetic energy 1/2 m sum v^2, and the
- * virial sum over pairs of d_ij . f_ij.  Rebuilds the list first if particles
+ * shifted to 0 at r_cut, plus FENE and angle terms), kinetic energy 1/2 m
+ * sum v^2, and the virial sum over pairs of d_ij . f_ij (the angle term,
+ * a function of the angle alone, has none).  Rebuilds the list first if particles
  * moved more than r_skin / 2 since the last build.  Asynchronous. */
 md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *stream);
 
@@ -154,7 +163,8 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
  * the current state, keeping (x, v) every ckpt_every steps in device memory the
  * handle owns, and write (U, K, W) per replica of the final state to euw_out
  * (3 * n_replicas FP64, host or device, may be NULL).  Pair potentials only:
- * returns MD_ERR_ARG for handles with FENE bonds or a thermostat.
+ * returns MD_ERR_ARG for handles with FENE bonds, angle triples, a thermostat
+ * or the push-off potential.
  * Synchronises `stream`. */
 md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *euw_out, void *stream);
 

@@ -8,6 +8,7 @@ What each function follows in arXiv:2109.10876:
   lj_energy / lj_force      Eq. 2 (LJ pair potential), F = -dV/dr (Eq. 1)
   soft_energy / soft_force  cosine push-off for overlapping chains (the melt of
                             Sec. 4 needs a preparation the paper leaves open)
+  angle_triple              cosine angle term on chain triples (Sec. 4)
   forces                    direct O(N^2) minimum-image pair sum under r < r_cut
   forces_sample             the same sum for chosen particles only
   pairs                     the Verlet pair set within r_cut + r_skin (Sec. 2.1.2)
@@ -43,6 +44,9 @@ class OrcSystem(C.Structure):
         ("fene_K", C.c_double),
         ("fene_R0", C.c_double),
         ("pot", C.c_int32),
+        ("angle_K", C.c_double),
+        ("n_angles", C.c_int64),
+        ("angles", C.POINTER(C.c_int32)),
     ]
 
 
@@ -61,6 +65,8 @@ def lib():
         L.orc_soft_energy.argtypes = [C.c_double, C.c_double, C.c_double]
         L.orc_soft_force.restype = C.c_double
         L.orc_soft_force.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.orc_angle_triple.restype = None
+        L.orc_angle_triple.argtypes = [dp, dp, dp, dp, C.c_double, dp, dp, dp, dp]
         L.orc_min_image_r2.restype = C.c_double
         L.orc_min_image_r2.argtypes = [dp, dp, dp]
         L.orc_forces.restype = C.c_int
@@ -112,7 +118,7 @@ class System:
 
     def __init__(self, n, box, eps=1.0, sigma=1.0, rc=2.5, shift=True, mass=1.0,
                  dt=0.005, gamma=0.0, kT=1.0, seed=0, bonds=None, fene_K=30.0,
-                 fene_R0=1.5, soft=False):
+                 fene_R0=1.5, soft=False, angles=None, angle_K=0.0):
         self.n = int(n)
         box = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)).copy()
         self.box = box
@@ -121,6 +127,8 @@ class System:
         self.bonds = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
         self.fene_K, self.fene_R0 = float(fene_K), float(fene_R0)
         self.soft = bool(soft)
+        self.angles = None if angles is None else np.ascontiguousarray(angles, dtype=np.int32).reshape(-1, 3)
+        self.angle_K = float(angle_K)
 
     def c(self):
         s = OrcSystem()
@@ -137,6 +145,13 @@ class System:
             s.bonds = C.POINTER(C.c_int32)()
         s.fene_K, s.fene_R0 = self.fene_K, self.fene_R0
         s.pot = 1 if self.soft else 0
+        s.angle_K = self.angle_K
+        if self.angles is not None and len(self.angles):
+            s.n_angles = len(self.angles)
+            s.angles = self.angles.ctypes.data_as(C.POINTER(C.c_int32))
+        else:
+            s.n_angles = 0
+            s.angles = C.POINTER(C.c_int32)()
         return s
 
 
@@ -154,6 +169,14 @@ def soft_energy(r, A=1.0, rc=2 ** (1 / 6)):
 
 def soft_force(r, A=1.0, rc=2 ** (1 / 6)):
     return lib().orc_soft_force(float(r), float(A), float(rc))
+
+
+def angle_triple(xa, xb, xc, box, K):
+    """Forces (fa, fb, fc) and energy of one cosine angle triple."""
+    xa, xb, xc, box = _f64(xa, 3), _f64(xb, 3), _f64(xc, 3), _f64(box, 3)
+    fa, fb, fc, u = np.zeros(3), np.zeros(3), np.zeros(3), np.zeros(1)
+    lib().orc_angle_triple(_dp(xa), _dp(xb), _dp(xc), _dp(box), float(K), _dp(fa), _dp(fb), _dp(fc), _dp(u))
+    return fa, fb, fc, float(u[0])
 
 
 def min_image_r2(xi, xj, box):

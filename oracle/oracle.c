@@ -24,6 +24,10 @@
  *     u uniform in (-1/2, 1/2) from Philox4x32-10 keyed by (seed) and counted by
  *     (particle id, step), applied with the velocity available at force time;
  *   - minimum image d -= L * nearbyint(d / L) per axis (valid for L >= 2 r_cut);
+ *   - the angle term on triples along a chain (Sec. 4 names a cosine-type
+ *     term on triples without its form) is U = K (1 - cos theta), theta
+ *     the angle between consecutive bond vectors b1 = x_b - x_a and
+ *     b2 = x_c - x_b (0 for a straight chain);
  *   - the soft push-off used to prepare overlapping polymer chains before the
  *     WCA melt run (Sec. 4 names the melt, not its preparation) is the cosine
  *     potential V = A (1 + cos(pi r / r_cut)) for r < r_cut, with A = eps.
@@ -62,6 +66,9 @@ typedef struct {
     const int32_t *bonds; /* 2*n_bonds particle ids, or NULL             */
     double fene_K, fene_R0;
     int32_t pot;          /* 0: LJ / WCA (Eq. 2), 1: soft cosine push-off  */
+    double angle_K;       /* bending constant of the angle term           */
+    int64_t n_angles;     /* angle triples (a, b, c), b the middle bead   */
+    const int32_t *angles;/* 3*n_angles particle ids, or NULL             */
 } orc_system;
 
 enum { ORC_OK = 0, ORC_ERR_BOND = -5, ORC_ERR_CAP = -3, ORC_ERR_ARG = -1 };
@@ -164,6 +171,43 @@ static int fene_pair(const orc_system *s, const double d[3], double r2,
     return ORC_OK;
 }
 
+/* Cosine angle term U = K (1 - cos theta) of one triple (a, b, c) with bond
+ * vectors b1 = x_b - x_a, b2 = x_c - x_b (minimum image), c = b1.b2/(l1 l2):
+ * F_a = -K (b2/(l1 l2) - c b1/l1^2), F_c = K (b1/(l1 l2) - c b2/l2^2),
+ * F_b = -(F_a + F_c).  U depends only on the angle, so its virial is zero. */
+double orc_angle_energy(const double b1[3], const double b2[3], double K)
+{
+    double l1 = sqrt(b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2]);
+    double l2 = sqrt(b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2]);
+    double c = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) / (l1 * l2);
+    return K * (1.0 - c);
+}
+
+static void angle_forces(const double b1[3], const double b2[3], double K,
+                         double fa[3], double fb[3], double fc[3])
+{
+    double l1s = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
+    double l2s = b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2];
+    double l12 = sqrt(l1s) * sqrt(l2s);
+    double c = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) / l12;
+    for (int k = 0; k < 3; ++k) {
+        fa[k] = -K * (b2[k] / l12 - c * b1[k] / l1s);
+        fc[k] = K * (b1[k] / l12 - c * b2[k] / l2s);
+        fb[k] = -(fa[k] + fc[k]);
+    }
+}
+
+/* Forces of the triple (a, b, c) at positions x (box L): fa, fb, fc and U. */
+void orc_angle_triple(const double *xa, const double *xb, const double *xc, const double *box, double K,
+                      double *fa, double *fb, double *fc, double *u)
+{
+    double b1[3], b2[3];
+    min_image(xb, xa, box, b1);
+    min_image(xc, xb, box, b2);
+    angle_forces(b1, b2, K, fa, fb, fc);
+    *u = orc_angle_energy(b1, b2, K);
+}
+
 /* ------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its          */
 /* published definition: 10 rounds of two 32x32->64 multiplies, with    */
@@ -259,6 +303,13 @@ int orc_forces(const orc_system *s, const double *x, const double *v,
         for (int k = 0; k < 3; ++k) { F[3 * i + k] += f[k]; F[3 * j + k] -= f[k]; }
         U += u;
         W += w;
+    }
+    for (int64_t t = 0; t < s->n_angles && s->angles; ++t) {
+        int64_t a = s->angles[3 * t], b = s->angles[3 * t + 1], c = s->angles[3 * t + 2];
+        double fa[3], fb[3], fc[3], u;
+        orc_angle_triple(&x[3 * a], &x[3 * b], &x[3 * c], s->box, s->angle_K, fa, fb, fc, &u);
+        for (int k = 0; k < 3; ++k) { F[3 * a + k] += fa[k]; F[3 * b + k] += fb[k]; F[3 * c + k] += fc[k]; }
+        U += u;
     }
     if (v) for (int64_t i = 0; i < n; ++i)
         K += 0.5 * s->mass * (v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2]);

@@ -334,6 +334,33 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
     if (tooclose) err |= kErrFixed;
 }
 
+// Cosine angle term K (1 - cos theta) of a triple (a, b, c) with bond vectors
+// b1 = x_b - x_a, b2 = x_c - x_b and c = b1.b2 / (|b1| |b2|): the force on the
+// particle of the given role, F_a = -K (b2/(l1 l2) - c b1/l1^2),
+// F_c = K (b1/(l1 l2) - c b2/l2^2), F_b = -(F_a + F_c); and the energy.
+template <class Real>
+__device__ __forceinline__ void angle_term(const Real b1[3], const Real b2[3], Real K, Real fa[3], Real fc[3], Real &u)
+{
+    const Real l1s = b1[0] * b1[0] + b1[1] * b1[1] + b1[2] * b1[2];
+    const Real l2s = b2[0] * b2[0] + b2[1] * b2[1] + b2[2] * b2[2];
+    const Real l12 = sqrt(l1s) * sqrt(l2s);
+    const Real c = (b1[0] * b2[0] + b1[1] * b2[1] + b1[2] * b2[2]) / l12;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        fa[k] = -K * (b2[k] / l12 - c * b1[k] / l1s);
+        fc[k] = K * (b1[k] / l12 - c * b2[k] / l2s);
+    }
+    u = K * (Real(1) - c);
+}
+
+// round(f 2^22) by the exact two-integer split
+__device__ __forceinline__ long long fx_round(float f)
+{
+    unsigned h = 0, l = 0;
+    fx_acc(f, h, l);
+    return (long long)(int)h * 4194304LL + (long long)(int)l;
+}
+
 // a4 + a5: forces on every particle of a tile from its Verlet list, with
 // the neighbour positions read from the tile's halo in shared memory, then
 // the velocity-Verlet update of that particle.  Persistent blocks take tiles
@@ -519,6 +546,45 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                             ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log(qd));
                             wi += 0.5 * c * r2;
                         }
+                    }
+                }
+            }
+            // angle triples of this particle (Sec. 4), every triple visited
+            // by its three particles; in FP32 mode the force joins the
+            // fixed-point sum
+            if (b.has_angles) {
+                const int id = (int)pi.w;
+                for (int q = b.ang_off[id]; q < b.ang_off[id + 1]; ++q) {
+                    const int4 e = b.ang_ent[q];
+                    const int sa = b.slot_of_id[e.x], sb = b.slot_of_id[e.y], sc = b.slot_of_id[e.z];
+                    if (PREC == 1) {
+                        const uint4 pa = P[sa], pb = P[sb], pcc = P[sc];
+                        const float b1[3] = {(float)(int)(pb.x - pa.x) * R.qs[0], (float)(int)(pb.y - pa.y) * R.qs[1],
+                                             (float)(int)(pb.z - pa.z) * R.qs[2]};
+                        const float b2[3] = {(float)(int)(pcc.x - pb.x) * R.qs[0], (float)(int)(pcc.y - pb.y) * R.qs[1],
+                                             (float)(int)(pcc.z - pb.z) * R.qs[2]};
+                        float fa[3], fc[3], u;
+                        angle_term<float>(b1, b2, b.angle_K_f, fa, fc, u);
+                        // the three visits round F_a and F_c identically and the
+                        // middle bead takes minus their sum: the triple adds exactly 0
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const long long qa = fx_round(fa[k]), qc = fx_round(fc[k]);
+                            Fd[k] += ll_to_double(e.w == 0 ? qa : (e.w == 2 ? qc : -(qa + qc)));
+                        }
+                        if (ENERGY) ui += (double)u / 3.0;
+                    } else {
+                        double b1[3], b2[3];
+                        for (int k = 0; k < 3; ++k) {
+                            double t1 = X[k * b.S + sb] - X[k * b.S + sa];
+                            double t2 = X[k * b.S + sc] - X[k * b.S + sb];
+                            b1[k] = t1 - R.L[k] * rint(t1 / R.L[k]);
+                            b2[k] = t2 - R.L[k] * rint(t2 / R.L[k]);
+                        }
+                        double fa[3], fc[3], u;
+                        angle_term<double>(b1, b2, b.angle_K, fa, fc, u);
+                        for (int k = 0; k < 3; ++k) Fd[k] += e.w == 0 ? fa[k] : (e.w == 2 ? fc[k] : -(fa[k] + fc[k]));
+                        if (ENERGY) ui += u / 3.0;
                     }
                 }
             }

@@ -424,6 +424,26 @@ md_status md_create(const md_params *p, md_handle **out)
         if (ra != rb) { delete h; return MD_ERR_ARG; }
     }
 
+    // angle triples: three distinct particles of one replica
+    if (p->n_angles < 0 || (p->n_angles > 0 && !p->angles) || (p->n_angles > 0 && !(p->angle_K >= 0))) {
+        delete h;
+        return MD_ERR_ARG;
+    }
+    for (int64_t q = 0; q < p->n_angles; ++q) {
+        long long id3[3];
+        int rr[3];
+        for (int k = 0; k < 3; ++k) {
+            id3[k] = p->angles[3 * q + k];
+            if (id3[k] < 0 || id3[k] >= h->N) { delete h; return MD_ERR_ARG; }
+            rr[k] = 0;
+            while (h->offsets[rr[k] + 1] <= id3[k]) ++rr[k];
+        }
+        if (id3[0] == id3[1] || id3[1] == id3[2] || id3[0] == id3[2] || rr[0] != rr[1] || rr[1] != rr[2]) {
+            delete h;
+            return MD_ERR_ARG;
+        }
+    }
+
     // list capacity: 1.5x the ideal-gas count in the list sphere at the
     // densest replica, plus a margin (grown on overflow by md_build_neighbors)
     int K = p->list_capacity;
@@ -549,6 +569,30 @@ md_status md_create(const md_params *p, md_handle **out)
         b.bond_off = doff;
         b.bond_partner = dpart;
         b.has_bonds = 1;
+    }
+    // angle triples as a per-particle list: every particle of a triple gets the
+    // whole triple and its role in it
+    if (p->n_angles > 0) {
+        std::vector<int> deg(h->N + 1, 0);
+        for (int64_t q = 0; q < p->n_angles; ++q)
+            for (int k = 0; k < 3; ++k) deg[p->angles[3 * q + k] + 1]++;
+        for (long long q = 0; q < h->N; ++q) deg[q + 1] += deg[q];
+        std::vector<int4> ent(3 * p->n_angles);
+        std::vector<int> fill(deg.begin(), deg.end() - 1);
+        for (int64_t q = 0; q < p->n_angles; ++q)
+            for (int k = 0; k < 3; ++k)
+                ent[fill[p->angles[3 * q + k]]++] =
+                    make_int4(p->angles[3 * q], p->angles[3 * q + 1], p->angles[3 * q + 2], k);
+        int *doff = dalloc<int>(h, h->N + 1);
+        int4 *dent = dalloc<int4>(h, ent.size());
+        if (!doff || !dent) { md_destroy(h); return MD_ERR_CUDA; }
+        ok &= cudaMemcpy(doff, deg.data(), sizeof(int) * (h->N + 1), cudaMemcpyHostToDevice) == cudaSuccess;
+        ok &= cudaMemcpy(dent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+        b.ang_off = doff;
+        b.ang_ent = dent;
+        b.has_angles = 1;
+        b.angle_K = p->angle_K;
+        b.angle_K_f = (float)p->angle_K;
     }
     if (!ok) { md_destroy(h); return MD_ERR_CUDA; }
     if (alloc_list(h, K) != MD_OK) { md_destroy(h); return MD_ERR_CUDA; }
@@ -774,8 +818,8 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
 {
     if (!h || nsteps < 0 || ckpt_every < 1) return fail(h, MD_ERR_ARG, "md_forward: bad arguments");
     if (!h->state_set) return fail(h, MD_ERR_ARG, "md_forward before md_set_state");
-    if (h->b.has_bonds || h->b.langevin || h->p.potential == MD_SOFT)
-        return fail(h, MD_ERR_ARG, "md_forward: the adjoint covers NVE LJ / WCA pair forces only (no bonds, thermostat or push-off)");
+    if (h->b.has_bonds || h->b.has_angles || h->b.langevin || h->p.potential == MD_SOFT)
+        return fail(h, MD_ERR_ARG, "md_forward: the adjoint covers NVE LJ / WCA pair forces only (no bonds, angles, thermostat or push-off)");
     cudaStream_t st = (cudaStream_t)stream;
     const long long n6 = 6LL * h->N;
     const long long nck = nsteps / ckpt_every + 1;

@@ -198,6 +198,11 @@ struct Bufs {
     const int *blk_rep;      // replica of every block of kBlock slots
     const int *bond_off;     // N + 1, bonds of particle id (both directions)
     const int *bond_partner; // 2 * n_bonds particle ids
+    const int *ang_off;      // N + 1: angle entries of particle id
+    const int4 *ang_ent;     // 3 * n_angles: (a, b, c, role of the particle: 0, 1, 2)
+    int has_angles;
+    double angle_K;
+    float angle_K_f;
     double *partial;         // 4 per tile: U, K, W partial sums
     double *thermo;          // where the last block writes (U, K, W) per replica, or null
     double *fout;            // force output in caller order (3 * N) or null

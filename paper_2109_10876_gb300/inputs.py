@@ -322,3 +322,29 @@ def sphere(n=2_580_000, L=271.0, rho=0.8442, T=0.1, seed=6):
     x = wrap(sites[np.sort(order)] + 0.5 * L, box)
     v = maxwell_velocities(n, T, seed)
     return x, v, box
+
+
+def rings(nring=1600, length=200, rho=0.85, T=1.0, seed=7, bond=0.97):
+    """Ring polymers (Sec. 4: rings of 200 beads at density 0.85): each ring a
+    closed random walk (bond steps of length `bond` in random directions, their
+    mean subtracted so that the walk closes), from a uniform random start;
+    overlaps are left for the soft push-off.  Returns (x, v, box, bonds
+    (nring length, 2), angles (nring length, 3): the triples (k-1, k, k+1) of
+    every ring, middle bead second)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = nring * length
+    L = (n / rho) ** (1.0 / 3.0)
+    box = np.array([L, L, L])
+    u = rng.standard_normal((nring, length, 3))
+    u *= bond / np.linalg.norm(u, axis=2, keepdims=True)
+    u -= u.mean(axis=1, keepdims=True)
+    walk = np.concatenate([np.zeros((nring, 1, 3)), np.cumsum(u[:, :-1], axis=1)], axis=1)
+    start = rng.uniform(0.0, L, size=(nring, 1, 3))
+    x = wrap((start + walk).reshape(-1, 3), box)
+    base = (np.arange(nring) * length)[:, None]
+    k = np.arange(length)[None, :]
+    bonds = np.stack([(base + k).ravel(), (base + (k + 1) % length).ravel()], axis=1).astype(np.int32)
+    angles = np.stack([(base + (k - 1) % length).ravel(), (base + k).ravel(),
+                       (base + (k + 1) % length).ravel()], axis=1).astype(np.int32)
+    v = maxwell_velocities(n, T, seed + 43)
+    return x, v, box, bonds, angles

@@ -57,6 +57,9 @@ class md_params(C.Structure):
         ("bonds", C.POINTER(C.c_int32)),
         ("list_capacity", C.c_int32),
         ("reserved0", C.c_int32),
+        ("angle_K", C.c_double),
+        ("n_angles", C.c_int64),
+        ("angles", C.POINTER(C.c_int32)),
     ]
 
 
@@ -184,7 +187,7 @@ class Handle:
 
 def md_create(n_per_replica, box, eps=1.0, sigma=1.0, rc_over_sigma=2.5, skin=0.3, dt=0.005, mass=1.0,
               potential=MD_LJ, precision=MD_FP32_FIXED, langevin_gamma=0.0, kT=1.0, seed=0,
-              fene_K=30.0, fene_R0=1.5, bonds=None, list_capacity=0):
+              fene_K=30.0, fene_R0=1.5, bonds=None, list_capacity=0, angles=None, angle_K=0.0):
     """md_create: n_per_replica is an int or a list of per-replica counts;
     box is (3,) or (R, 3); eps, sigma scalars or per replica."""
     sizes = np.atleast_1d(np.asarray(n_per_replica, dtype=np.int64))
@@ -217,11 +220,17 @@ def md_create(n_per_replica, box, eps=1.0, sigma=1.0, rc_over_sigma=2.5, skin=0.
         p.n_bonds = len(bonda)
         p.bonds = bonda.ctypes.data_as(C.POINTER(C.c_int32))
     p.list_capacity = list_capacity
+    anga = None
+    if angles is not None and len(angles):
+        anga = np.ascontiguousarray(angles, dtype=np.int32).reshape(-1, 3)
+        p.n_angles = len(anga)
+        p.angles = anga.ctypes.data_as(C.POINTER(C.c_int32))
+        p.angle_K = angle_K
     h = _H()
     st = _lib.md_create(C.byref(p), C.byref(h))
     if st != MD_OK:
         raise MDError(st, "md_create failed")
-    return Handle(h, (off, boxa, epsa, siga, bonda))
+    return Handle(h, (off, boxa, epsa, siga, bonda, anga))
 
 
 def md_destroy(h):

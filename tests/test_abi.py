@@ -3,6 +3,7 @@ and rejects bad parameters on the host (no GPU needed)."""
 import ctypes as C
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -36,9 +37,30 @@ def test_every_declared_symbol_is_exported(md):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 
 
-def test_params_struct_matches_header_size(md):
-    # md_params: the ctypes mirror must have the C layout (pointers 8 B, natural alignment)
-    assert C.sizeof(md.md_params) == 4 + 4 + 8 * 4 + 8 * 4 + 4 + 4 + 8 * 2 + 8 + 8 * 2 + 8 + 8 + 4 + 4
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of `struct` from the C compiler reading include/md.h."""
+    inc = os.path.join(ROOT, "include")
+    src = tmp_path / "layout.c"
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "md.h"', "int main(void) {",
+             f'    printf("%zu\\n", sizeof({struct}));']
+    lines += [f'    printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["    return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    return int(out[0]), [int(t) for t in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["md_params", "md_stats"])
+def test_structs_match_the_header_layout(md, name, tmp_path):
+    """The ctypes mirrors have the C layout of include/md.h: size and every
+    field offset, as the C compiler computes them."""
+    st = getattr(md, name)
+    fields = [f for f, _ in st._fields_]
+    size, offs = _c_layout(name, fields, tmp_path)
+    assert C.sizeof(st) == size
+    assert [getattr(st, f).offset for f in fields] == offs
 
 
 def test_box_too_small_and_bad_args_are_rejected_on_host(md):

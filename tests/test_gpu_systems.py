@@ -200,3 +200,68 @@ def test_soft_pushoff_needs_fp64(md):
     x, v, box, bonds = inputs.melt(nchain=4, nbead=10, rho=0.85, seed=42)
     with pytest.raises(md.MDError):
         md.md_create(len(x), box, potential=md.MD_SOFT, rc_over_sigma=2 ** (1 / 6), precision=1)
+
+
+def test_rings_with_angles_fp64(md):
+    """Ring polymers (Sec. 4) under the push-off with FENE bonds, the cosine
+    angle term and the Langevin thermostat: forces and energies match the
+    oracle, and 20 steps follow its trajectory."""
+    x, v, box, bonds, angles = inputs.rings(8, 30, rho=0.6, seed=51)
+    n = len(x)
+    rc = 2 ** (1 / 6)
+    kw = dict(potential=md.MD_SOFT, rc_over_sigma=rc, eps=5.0, skin=0.4, bonds=bonds, angles=angles,
+              angle_K=1.5, dt=0.005, langevin_gamma=0.5, kT=1.0, seed=5)
+    h = md.md_create(n, box, precision=0, **kw)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    f = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+    euw = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, euw)
+    md.md_sync(h)
+    s = oracle.System(n, box, eps=5.0, rc=rc, soft=True, bonds=bonds, angles=angles, angle_K=1.5, dt=0.005,
+                      gamma=0.5, kT=1.0, seed=5)
+    Fo, eo = oracle.forces(s, x, v)
+    assert force_rel_err(host(f), Fo) <= 1e-12
+    np.testing.assert_allclose(euw.cpu().numpy()[0], eo, rtol=1e-12, atol=1e-12 * n)
+    md.md_step(h, 20)
+    xo = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+    vo = torch.zeros_like(xo)
+    md.md_get_state(h, xo, vo)
+    x1, v1, _ = oracle.vv_run(s, x, v, 20)
+    assert np.max(np.abs(min_image_diff(host(xo), x1, box))) < 1e-10
+    assert np.max(np.abs(host(vo) - v1)) < 1e-9
+
+
+def test_chains_wca_fene_angles_fp32(md):
+    """Self-avoiding linear chains with WCA, FENE and the angle term on every
+    interior triple, FP32 pairs and fixed-point sums: forces and energies
+    within 1e-5 of the oracle, and the total force is exactly zero."""
+    box = np.array([9.0, 9.0, 9.0])
+    x, bonds = inputs.chains(12, 25, box, seed=52)
+    n = len(x)
+    v = inputs.maxwell_velocities(n, 1.0, 53)
+    angles = np.array([(c * 25 + k - 1, c * 25 + k, c * 25 + k + 1) for c in range(12) for k in range(1, 24)],
+                      dtype=np.int32)
+    kw = dict(potential=md.MD_WCA, skin=0.4, bonds=bonds, fene_K=30.0, fene_R0=1.5, angles=angles, angle_K=1.5)
+    h = md.md_create(n, box, precision=1, **kw)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    f = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+    euw = torch.zeros(1, 3, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, euw)
+    md.md_sync(h)
+    s = oracle.System(n, box, rc=2 ** (1 / 6), bonds=bonds, fene_K=30.0, fene_R0=1.5, angles=angles, angle_K=1.5)
+    Fo, eo = oracle.forces(s, x, v)
+    F = host(f)
+    assert force_rel_err(F, Fo) <= 1e-5
+    np.testing.assert_allclose(euw.cpu().numpy()[0], eo, rtol=1e-5, atol=1e-5 * n)
+    assert np.all(F.sum(axis=0) == 0.0)
+
+
+def test_angles_rejected_by_the_adjoint(md):
+    x, v, box, bonds, angles = inputs.rings(2, 10, rho=0.2, seed=54)
+    h = md.md_create(len(x), box, precision=0, potential=md.MD_WCA, bonds=bonds, angles=angles, angle_K=1.0)
+    md.md_set_state(h, dev(x), dev(v))
+    with pytest.raises(md.MDError) as e:
+        md.md_forward(h, 2, 1, np.zeros(3))
+    assert e.value.status == md.MD_ERR_ARG

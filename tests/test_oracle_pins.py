@@ -424,3 +424,63 @@ def test_soft_pushoff_force_is_minus_grad_U_and_nve_second_order():
         th = oracle.vv_run(s, x, v, int(round(0.4 / dt)), thermo=True)[3]
         dE.append(np.max(np.abs(th[:, 0] + th[:, 1] - e0[0] - e0[1])))
     assert 3.0 < dE[0] / dE[1] < 5.0
+
+
+# ---------------------------------------------------------------- angle term
+def test_angle_term_closed_forms_and_sympy_gradient():
+    """Cosine angle term K (1 - cos theta) between consecutive bond vectors:
+    zero force on a straight triple; the right angle gives U = K and forces
+    along the other bond; at random triples the forces are sympy's
+    -grad U, sum to zero, exert no torque and have zero virial."""
+    box = np.array([20.0, 20.0, 20.0])
+    K = 1.5
+    fa, fb, fc, u = oracle.angle_triple([1, 1, 1], [2, 1, 1], [3, 1, 1], box, K)
+    assert u == 0.0 and np.all(np.abs(np.concatenate([fa, fb, fc])) < 1e-15)
+    fa, fb, fc, u = oracle.angle_triple([1, 1, 1], [2, 1, 1], [2, 3, 1], box, K)
+    assert u == pytest.approx(K, rel=1e-15)
+    np.testing.assert_allclose(fa, [0, -K, 0], atol=1e-15)     # |b2| = 2 scales out of fa's direction only
+    np.testing.assert_allclose(fc, [K / 2, 0, 0], atol=1e-15)
+    for theta in (0.3, 1.0, 2.0, 3.0):
+        xc = [2 + np.cos(theta), 1 + np.sin(theta), 1]
+        assert oracle.angle_triple([1, 1, 1], [2, 1, 1], xc, box, K)[3] == pytest.approx(K * (1 - np.cos(theta)), rel=1e-13)
+    X = sp.symbols("ax ay az bx by bz cx cy cz")
+    a, b, c = sp.Matrix(X[0:3]), sp.Matrix(X[3:6]), sp.Matrix(X[6:9])
+    b1, b2 = b - a, c - b
+    U = K * (1 - b1.dot(b2) / (sp.sqrt(b1.dot(b1)) * sp.sqrt(b2.dot(b2))))
+    grad = sp.lambdify(X, [-sp.diff(U, q) for q in X], "mpmath")
+    rng = np.random.default_rng(8)
+    for _ in range(10):
+        pts = 5 + rng.uniform(-1, 1, (3, 3))
+        fa, fb, fc, u = oracle.angle_triple(pts[0], pts[1], pts[2], box, K)
+        want = np.array([float(g) for g in grad(*pts.ravel())])
+        np.testing.assert_allclose(np.concatenate([fa, fb, fc]), want, rtol=1e-11, atol=1e-12)
+        F = np.stack([fa, fb, fc])
+        assert np.max(np.abs(F.sum(axis=0))) < 1e-12
+        assert np.max(np.abs(np.cross(pts - pts[1], F).sum(axis=0))) < 1e-12
+        assert abs(np.sum((pts - pts[1]) * F)) < 1e-12
+
+
+def test_angle_term_in_forces_and_nve():
+    """Rings with FENE, the soft push-off and the angle term: forces are -grad U by
+    central differences across the periodic boundary, and velocity Verlet
+    conserves energy to second order."""
+    x, v, box, bonds, angles = inputs.rings(3, 12, rho=0.3, seed=9)
+    n = len(x)
+    s = oracle.System(n, box, eps=5.0, rc=2 ** (1 / 6), soft=True, bonds=bonds, angles=angles, angle_K=1.5, dt=0.002)
+    F, euw = oracle.forces(s, x)
+    assert np.max(np.abs(F.sum(axis=0))) < 1e-10 * max(1.0, np.max(np.abs(F)))
+    h = 1e-6
+    for i in (0, 5, 17, 30):
+        for k in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, k] += h
+            xm[i, k] -= h
+            d = -(oracle.forces(s, xp)[1][0] - oracle.forces(s, xm)[1][0]) / (2 * h)
+            assert F[i, k] == pytest.approx(d, abs=1e-5 * max(1.0, abs(F[i, k])))
+    dE = []
+    for dt in (0.002, 0.001):
+        s = oracle.System(n, box, eps=5.0, rc=2 ** (1 / 6), soft=True, bonds=bonds, angles=angles, angle_K=1.5, dt=dt)
+        e0 = oracle.forces(s, x, v)[1]
+        th = oracle.vv_run(s, x, v, int(round(0.2 / dt)), thermo=True)[3]
+        dE.append(np.max(np.abs(th[:, 0] + th[:, 1] - e0[0] - e0[1])))
+    assert 3.0 < dE[0] / dE[1] < 5.0
