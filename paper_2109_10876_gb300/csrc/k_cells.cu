@@ -199,7 +199,11 @@ __global__ void k_cond(Ctl *ctl, cudaGraphConditionalHandle handle, int what)
     cudaGraphSetConditional(handle, v ? 1u : 0u);
 }
 
-__global__ void k_set_steps(Ctl *ctl, long long left) { ctl->steps_left = left; }
+__global__ void k_set_steps(Ctl *ctl, long long left)
+{
+    ctl->steps_left = left;
+    ctl->rec = 0;
+}
 
 // ---------------------------------------------------------------- counting sort
 // a1: cell id of every particle and the cell histogram.

@@ -230,7 +230,13 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, flo
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (energy) reduce_partials(b, b.thermo);
+    if (energy) {
+        // a graph-launched md_step records every step into its ring slot
+        double *out = b.thermo;
+        if (!out && b.thermo_ring) out = b.thermo_ring + 3 * (long long)b.nrep * b.ctl->rec;
+        reduce_partials(b, out);
+        if (!b.thermo && b.thermo_ring && threadIdx.x == 0) b.ctl->rec += 1;
+    }
     if (threadIdx.x == 0) {
         if (drifted) {
             unsigned bits = atomicExch(&b.ctl->disp2_bits, 0u);

@@ -53,8 +53,9 @@ struct md_handle {
     // the step loop as a CUDA graph (conditional WHILE over steps, IF over rebuilds)
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    long long gen = 0, gexec_gen = -1;   // bumped whenever the kernels' buffers change
+    cudaGraphExec_t gexec = nullptr, gexec_e = nullptr;       // without / with energies every step
+    cudaGraph_t graph_e = nullptr;
+    long long gen = 0, gexec_gen = -1, gexec_e_gen = -1;   // gen: bumped whenever the kernels' buffers change
     bool use_graph = true;
 };
 
@@ -143,6 +144,7 @@ md_status ensure_thermo(md_handle *h, long long count)
     h->thermo_stage = dalloc<double>(h, (size_t)count);
     if (!h->thermo_stage) return fail(h, MD_ERR_CUDA, "cannot allocate thermo buffer");
     h->thermo_cap = count;
+    h->gen++;   // the energy graph holds the buffer's address
     return MD_OK;
 }
 
@@ -224,24 +226,32 @@ bool capture_into(md_handle *h, cudaGraph_t g, const std::vector<cudaGraphNode_t
     return cudaStreamEndCapture(h->cap, &out) == cudaSuccess;
 }
 
-// One graph for md_step(n > 0) without timers or energies:
+// One graph for md_step(n > 0) without timers, without energies or with
+// energies every step (`energy`):
 //   kick-drift -> cond(W: steps left) -> WHILE(W) { cond(I: rebuild) -> IF(I) { rebuild chain }
 //   -> fused force } -> cond(I2) -> IF(I2) { rebuild chain } -> final force.
-// The fused kernel's last block counts the steps down and sets W.
-bool build_step_graph(md_handle *h)
+// The fused kernel's last block counts the steps down and sets W; with
+// energies, each force kernel's last block writes its record to the next slot
+// of the thermo buffer.
+bool build_step_graph(md_handle *h, bool energy)
 {
-    if (h->gexec && h->gexec_gen == h->gen) return true;
-    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    cudaGraphExec_t &gexec = energy ? h->gexec_e : h->gexec;
+    cudaGraph_t &graph = energy ? h->graph_e : h->graph;
+    long long &ggen = energy ? h->gexec_e_gen : h->gexec_gen;
+    if (gexec && ggen == h->gen) return true;
+    if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+    if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return false;
     cudaGraph_t G;
     if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
-    h->graph = G;
+    graph = G;
     cudaGraphConditionalHandle hW, hI2;
     if (cudaGraphConditionalHandleCreate(&hW, G, 0, 0) != cudaSuccess) return false;
     if (cudaGraphConditionalHandleCreate(&hI2, G, 0, 0) != cudaSuccess) return false;
     Bufs b = h->b;
     b.g_while = 0;
+    b.thermo = nullptr;
+    b.thermo_ring = energy ? h->thermo_stage : nullptr;
     const int prec = h->precision;
     std::vector<cudaGraphNode_t> tail;
     if (!capture_into(h, G, {}, [&](cudaStream_t s) {
@@ -272,7 +282,7 @@ bool build_step_graph(md_handle *h)
         return false;
     Bufs bf = b;
     bf.g_while = hW;
-    if (!capture_into(h, BW, {nI}, [&](cudaStream_t s) { mdk::launch_force(bf, prec, mdk::kModeFused, false, s); },
+    if (!capture_into(h, BW, {nI}, [&](cudaStream_t s) { mdk::launch_force(bf, prec, mdk::kModeFused, energy, s); },
                       nullptr))
         return false;
     if (!capture_into(h, G, {nW}, [&](cudaStream_t s) { mdk::launch_cond(b, hI2, 0, s); }, &tail)) return false;
@@ -286,11 +296,11 @@ bool build_step_graph(md_handle *h)
     if (!capture_into(h, ip2.conditional.phGraph_out[0], {}, [&](cudaStream_t s) { mdk::launch_rebuild_chain(b, s); },
                       nullptr))
         return false;
-    if (!capture_into(h, G, {nI2}, [&](cudaStream_t s) { mdk::launch_force(b, prec, mdk::kModeFinal, false, s); },
+    if (!capture_into(h, G, {nI2}, [&](cudaStream_t s) { mdk::launch_force(b, prec, mdk::kModeFinal, energy, s); },
                       nullptr))
         return false;
-    if (cudaGraphInstantiate(&h->gexec, G, 0) != cudaSuccess) { h->gexec = nullptr; return false; }
-    h->gexec_gen = h->gen;
+    if (cudaGraphInstantiate(&gexec, G, 0) != cudaSuccess) { gexec = nullptr; return false; }
+    ggen = h->gen;
     return true;
 }
 
@@ -608,6 +618,8 @@ void md_destroy(md_handle *h)
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->gexec_e) cudaGraphExecDestroy(h->gexec_e);
+    if (h->graph_e) cudaGraphDestroy(h->graph_e);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -719,14 +731,19 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
     const long long nrec = thermo_every > 0 ? nsteps / thermo_every : 0;
     if (nrec > 0 && ensure_thermo(h, nrec * 3 * nrep) != MD_OK) return MD_ERR_CUDA;
     Bufs b = h->b;
-    if (!h->timing && nrec == 0 && h->use_graph && build_step_graph(h)) {
+    const bool every = nrec > 0 && thermo_every == 1;
+    if (!h->timing && (nrec == 0 || every) && h->use_graph && build_step_graph(h, every)) {
         if (!h->F_valid) {
             mdk::launch_rebuild_chain(b, st);
             mdk::launch_force(b, h->precision, mdk::kModeStore, false, st);
         }
         mdk::launch_set_steps(b, (long long)nsteps - 1, st);
-        if (!cuda_ok(h, cudaGraphLaunch(h->gexec, st), "graph launch")) return MD_ERR_CUDA;
+        if (!cuda_ok(h, cudaGraphLaunch(every ? h->gexec_e : h->gexec, st), "graph launch")) return MD_ERR_CUDA;
         h->F_valid = true;
+        if (every &&
+            !cuda_ok(h, cudaMemcpyAsync(thermo_out, h->thermo_stage, sizeof(double) * nrec * 3 * nrep,
+                                        cudaMemcpyDefault, st), "copy thermo out"))
+            return MD_ERR_CUDA;
         return MD_OK;
     }
     cudaGetLastError();   // a failed graph build leaves nothing behind: fall back to stream launches

@@ -93,6 +93,7 @@ struct Ctl {
     int max_halo;            // largest halo of the current build
     long long step;          // index of the current positions x_step
     long long steps_left;    // fused steps still to run in a graph-launched md_step
+    long long rec;           // energy records written by this graph-launched md_step
     long long rebuilds;
     long long list_entries;
 };
@@ -205,6 +206,7 @@ struct Bufs {
     float angle_K_f;
     double *partial;         // 4 per tile: U, K, W partial sums
     double *thermo;          // where the last block writes (U, K, W) per replica, or null
+    double *thermo_ring;     // graph-launched md_step: record Ctl::rec goes to thermo_ring + 3 nrep rec
     double *fout;            // force output in caller order (3 * N) or null
     Ctl *ctl;
     long long S, N;

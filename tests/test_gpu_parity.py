@@ -201,3 +201,26 @@ def test_automatic_capacity_grows(md):
     got = md.export_pairs_sorted(h)
     want, _ = oracle.pairs(oracle.System(len(x), box, rc=RC), x, RC + SKIN)
     np.testing.assert_array_equal(got, want)
+
+
+def test_thermo_every_step_graph_equals_stream_launches(md):
+    """md_step with (U, K, W) every step runs as one graph launch; with the
+    section timers on the same kernels are launched one by one.  Both give
+    the same records and the same state, bit for bit, and the records follow
+    the oracle's energies."""
+    x, v, box = inputs.perturbed_lattice(6, seed=17, amp=0.1)
+    n = len(x)
+    out = []
+    for timing in (False, True):
+        h = make(md, x, v, box, 1)
+        md.md_set_timing(h, timing)
+        th = np.zeros((30, 3))
+        md.md_step(h, 30, 1, th)
+        xo = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+        vo = torch.zeros_like(xo)
+        md.md_get_state(h, xo, vo)
+        out.append((th.copy(), xo.cpu().numpy(), vo.cpu().numpy()))
+    for a, b in zip(out[0], out[1]):
+        np.testing.assert_array_equal(a, b)
+    xo, vo, Fo, tho = oracle.vv_run(oracle.System(n, box, rc=RC, dt=0.005), x, v, 30, thermo=True)
+    np.testing.assert_allclose(out[0][0], tho, rtol=1e-5, atol=1e-5 * n)
