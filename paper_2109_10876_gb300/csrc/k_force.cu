@@ -63,12 +63,6 @@ __device__ __forceinline__ void fx_acc(float f, unsigned &hi, unsigned &lo)
     lo += __float_as_uint(t2) - kMagicBits;
 }
 
-__device__ __forceinline__ double fx_value(unsigned hi, unsigned lo)
-{
-    long long v = (long long)(int)hi * 4194304LL + (long long)(int)lo;
-    return ll_to_double(v) * kFixInv;
-}
-
 __device__ __forceinline__ double wrap1(double y, double L)
 {
     if (y >= L) y = y - L;
@@ -143,12 +137,59 @@ __device__ __forceinline__ void block_sum3(double &a, double &c, double &d, doub
     }
 }
 
+// Block-wide sum of three 64-bit integers; exact, result valid in thread 0.
+__device__ __forceinline__ void block_sum3_ll(long long &a, long long &c, long long &d, long long (*sm)[3])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+        d += __shfl_down_sync(0xffffffffu, d, o);
+    }
+    int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sm[w][0] = a; sm[w][1] = c; sm[w][2] = d; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = c = d = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += sm[q][0]; c += sm[q][1]; d += sm[q][2]; }
+    }
+}
+
 // Last block: per-replica totals from the per-tile partials, in tile order.
-__device__ void reduce_partials(const Bufs &b, double *thermo)
+// `fixed`: the partials are 64-bit integers, twice the energies in units of
+// 2^-22 (the FP32 path's exact, order-independent sums).
+__device__ void reduce_partials(const Bufs &b, double *thermo, bool fixed)
 {
     __shared__ double red[kBlock][3];
+    const long long *pl = reinterpret_cast<const long long *>(b.partial);
     for (int r = 0; r < b.nrep; ++r) {
         double a = 0, c = 0, d = 0;
+        if (fixed) {
+            long long la = 0, lc = 0, ld = 0;
+            for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x) {
+                la += pl[4 * q + 0];
+                lc += pl[4 * q + 1];
+                ld += pl[4 * q + 2];
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                la += __shfl_down_sync(0xffffffffu, la, o);
+                lc += __shfl_down_sync(0xffffffffu, lc, o);
+                ld += __shfl_down_sync(0xffffffffu, ld, o);
+            }
+            __shared__ long long redl[kBlock / 32][3];
+            if ((threadIdx.x & 31) == 0) { redl[threadIdx.x >> 5][0] = la; redl[threadIdx.x >> 5][1] = lc; redl[threadIdx.x >> 5][2] = ld; }
+            __syncthreads();
+            if (threadIdx.x == 0 && thermo) {
+                la = lc = ld = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { la += redl[w][0]; lc += redl[w][1]; ld += redl[w][2]; }
+                constexpr double half_unit = 0.5 / 4194304.0;
+                thermo[3 * r + 0] = half_unit * ll_to_double(la);
+                thermo[3 * r + 1] = half_unit * ll_to_double(lc);
+                thermo[3 * r + 2] = half_unit * ll_to_double(ld);
+            }
+            __syncthreads();
+            continue;
+        }
         for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x) {
             a += b.partial[4 * q + 0];
             c += b.partial[4 * q + 1];
@@ -217,7 +258,7 @@ __device__ __forceinline__ float block_max(float v, float *sm)
 // End-of-kernel bookkeeping by the last block to finish: energy totals, the
 // work counter, and for kernels that drifted the buffer flip, the step
 // counter and the rebuild decision for the next step.
-__device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, float ratio_blk)
+__device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, float ratio_blk, bool fixed = false)
 {
     if (!drifted && !energy && !tiled) return;
     __shared__ bool last;
@@ -234,7 +275,7 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, flo
         // a graph-launched md_step records every step into its ring slot
         double *out = b.thermo;
         if (!out && b.thermo_ring) out = b.thermo_ring + 3 * (long long)b.nrep * b.ctl->rec;
-        reduce_partials(b, out);
+        reduce_partials(b, out, fixed);
         if (!b.thermo && b.thermo_ring && threadIdx.x == 0) b.ctl->rec += 1;
     }
     if (threadIdx.x == 0) {
@@ -380,6 +421,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     __shared__ int s_tile, s_np, s_self;
     __shared__ int s_nn[kTileMax];
     __shared__ double sm3[kBlock / 32][3];
+    __shared__ long long sml[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
     if (block_uniform(b.ctl->err != 0)) return;
     const int cur = b.ctl->cur, nxt = cur ^ 1;
@@ -436,6 +478,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         cp_async_wait_all();
         __syncthreads();
         double ui = 0.0, wi = 0.0, ki = 0.0;
+        // FP32 path: energies as integers, twice the energy in units of 2^-22
+        long long uf = 0, wf = 0, kf = 0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
             if (MODE == kModeFused) {
                 // this particle's integration state, needed after the pair loop
@@ -464,7 +508,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 for (int k = 0; k < 3; ++k)
                     Fd[k] = ll_to_double((long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k]);
                 fscale = kFixInv;
-                if (ENERGY) { ui += 0.5 * fx_value(a.hu, a.lu); wi += 0.5 * fx_value(a.hw, a.lw); }
+                if (ENERGY) {
+                    uf += (long long)(int)a.hu * 4194304LL + (long long)(int)a.lu;
+                    wf += (long long)(int)a.hw * 4194304LL + (long long)(int)a.lw;
+                }
             } else {
                 const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
                 const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
@@ -534,8 +581,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                         fx_acc2(c, dy, h, l); Fd[1] += ll_to_double((long long)(int)h * 4194304LL + (long long)(int)l); h = l = 0;
                         fx_acc2(c, dz, h, l); Fd[2] += ll_to_double((long long)(int)h * 4194304LL + (long long)(int)l);
                         if (ENERGY) {
-                            ui += 0.5 * (-0.5 * b.fene_K * b.fene_R02 * log((double)qf));
-                            wi += 0.5 * (double)(c * r2);
+                            uf += fix_round(-0.5 * b.fene_K * b.fene_R02 * log((double)qf), 4194304.0);
+                            wf += fix_round((double)(c * r2), 4194304.0);
                         }
                     } else {
                         double d[3];
@@ -578,7 +625,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                             const long long qa = fx_round(fa[k]), qc = fx_round(fc[k]);
                             Fd[k] += ll_to_double(e.w == 0 ? qa : (e.w == 2 ? qc : -(qa + qc)));
                         }
-                        if (ENERGY) ui += (double)u / 3.0;
+                        if (ENERGY) uf += fix_round(2.0 * (double)u / 3.0, 4194304.0);
                     } else {
                         double b1[3], b2[3];
                         for (int k = 0; k < 3; ++k) {
@@ -608,32 +655,56 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 const int id = (int)pi.w;
                 if (b.fout)
                     for (int k = 0; k < 3; ++k) b.fout[k * b.N + id] = Fd[k] * fscale;
-                if (ENERGY)
-                    for (int k = 0; k < 3; ++k) { double w = b.v[cur][k * b.S + i]; ki += 0.5 * b.mass * w * w; }
+                if (ENERGY) {
+                    double w2 = 0.0;
+                    for (int k = 0; k < 3; ++k) { double w = b.v[cur][k * b.S + i]; w2 += w * w; }
+                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    else ki += 0.5 * b.mass * w2;
+                }
             } else if (MODE == kModeStore) {
                 for (int k = 0; k < 3; ++k) b.F[k * b.S + i] = Fd[k] * fscale;
-                if (ENERGY) for (int k = 0; k < 3; ++k) ki += 0.5 * b.mass * v[k] * v[k];
+                if (ENERGY) {
+                    const double w2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    else ki += 0.5 * b.mass * w2;
+                }
             } else if (MODE == kModeFinal) {
                 const double c = b.half_dt_over_m * fscale;
                 for (int k = 0; k < 3; ++k) {
                     v[k] += c * Fd[k];
                     b.v[cur][k * b.S + i] = v[k];
                     b.F[k * b.S + i] = Fd[k] * fscale;
-                    if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
+                }
+                if (ENERGY) {
+                    const double w2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    else ki += 0.5 * b.mass * w2;
                 }
             } else {  // kModeFused: end of step n, then the first half kick and drift of step n + 1
                 const double c = b.half_dt_over_m * fscale;
                 double xi[3];
+                for (int k = 0; k < 3; ++k) v[k] += c * Fd[k];
+                if (ENERGY) {
+                    const double w2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    else ki += 0.5 * b.mass * w2;
+                }
                 for (int k = 0; k < 3; ++k) {
-                    v[k] += c * Fd[k];
-                    if (ENERGY) ki += 0.5 * b.mass * v[k] * v[k];
                     v[k] += c * Fd[k];
                     xi[k] = X[k * b.S + i];
                 }
                 ratio = fmaxf(ratio, drift(b, R, i, nxt, pi.w, xi, v));
             }
         }
-        if (ENERGY) {
+        if (ENERGY && PREC == 1) {
+            block_sum3_ll(uf, kf, wf, sml);
+            if (threadIdx.x == 0) {
+                long long *pl = reinterpret_cast<long long *>(b.partial);
+                pl[4 * t + 0] = uf;
+                pl[4 * t + 1] = kf;
+                pl[4 * t + 2] = wf;
+            }
+        } else if (ENERGY) {
             double a = ui, c = ki, d = wi;
             block_sum3(a, c, d, sm3);
             if (threadIdx.x == 0) {
@@ -648,7 +719,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     if (err) atomicOr(&b.ctl->err, err);
     constexpr bool kDrift = (MODE == kModeFused);
     if (kDrift) ratio = block_max(ratio, smr);
-    finish(b, kDrift, ENERGY, true, ratio);
+    finish(b, kDrift, ENERGY, true, ratio, PREC == 1);
 }
 
 // Integrate1 of the first step of an md_step call: v += dt/2m F; x += dt v.
