@@ -63,6 +63,14 @@ __device__ __forceinline__ void fx_acc(float f, unsigned &hi, unsigned &lo)
     lo += __float_as_uint(t2) - kMagicBits;
 }
 
+// round(f 2^22) by the exact two-integer split
+__device__ __forceinline__ long long fx_round(float f)
+{
+    unsigned h = 0, l = 0;
+    fx_acc(f, h, l);
+    return (long long)(int)h * 4194304LL + (long long)(int)l;
+}
+
 __device__ __forceinline__ double wrap1(double y, double L)
 {
     if (y >= L) y = y - L;
@@ -298,7 +306,12 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, flo
 // FP32 pair terms of one neighbour: LJ force scalar masked to zero unless
 // `in`, and the fixed-point accumulation of force, energy and virial.
 struct Acc32 {
-    unsigned hx, lx, hy, ly, hz, lz, hu, lu, hw, lw;
+    unsigned hx, lx, hy, ly, hz, lz;
+    // energies: sums over the interacting pairs of s6 (s6 - 1) and
+    // s6 (2 s6 - 1) (s6 = (sigma/r)^6) and their count, so that the pair
+    // energy is 4 eps su - n V(r_cut) and the virial 24 eps sg
+    float su, sg;
+    int nin;
 };
 
 // slot of halo index h (pieces are in ascending halo order)
@@ -313,7 +326,7 @@ __device__ __forceinline__ int halo_slot(const Piece *pc, int np, int h)
 // scalar fs in force / u (constants pre-scaled), so fs * d is the force.
 template <bool ENERGY>
 __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, bool in, float sig2, float eps24,
-                                       float eps24p, float eps4, float vsh, Acc32 &a)
+                                       Acc32 &a)
 {
     const float ir2 = rcp_approx(r2);
     const float s2 = sig2 * ir2;
@@ -324,8 +337,9 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, b
     fx_acc2(fs, dy, a.hy, a.ly);
     fx_acc2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        fx_acc(in ? eps4 * s6 * (s6 - 1.0f) - vsh : 0.0f, a.hu, a.lu);   // V(r) - V(r_cut)
-        fx_acc(in ? eps24p * g : 0.0f, a.hw, a.lw);                      // r f(r) = d . f
+        a.su += in ? s6 * (s6 - 1.0f) : 0.0f;
+        a.sg += in ? g : 0.0f;
+        a.nin += in ? 1 : 0;
     }
 }
 
@@ -349,7 +363,7 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
 {
     const float ry = R.ry, rz = R.rz;
     const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
-    const float sig2 = R.sig2_u, eps24 = R.eps24_u, eps24p = R.eps24_f, eps4 = R.eps4_f, vsh = R.vshift_f;
+    const float sig2 = R.sig2_u, eps24 = R.eps24_u;
     int nband = 0;
     bool tooclose = false;
     for (int k0 = 0; k0 < npad; k0 += kU) {
@@ -364,7 +378,7 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
             const bool in = (r2 < lo) & nz;
             nband += (r2 < hi) & !(r2 < lo);
             tooclose |= (r2 < fmax2) & nz;
-            pair32<ENERGY>(dx, dy, dz, r2, in, sig2, eps24, eps24p, eps4, vsh, a);
+            pair32<ENERGY>(dx, dy, dz, r2, in, sig2, eps24, a);
         }
     }
     if (nband) {
@@ -375,7 +389,7 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
             float dx, dy, dz, r2;
             sep_u<CUBIC>(pi, hpos[h], ry, rz, dx, dy, dz, r2);
             if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, halo_slot(pc, np, h), R.L) < R.rc2)
-                pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, eps24p, eps4, vsh, a);
+                pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, a);
         }
     }
     if (tooclose) err |= kErrFixed;
@@ -400,13 +414,6 @@ __device__ __forceinline__ void angle_term(const Real b1[3], const Real b2[3], R
     u = K * (Real(1) - c);
 }
 
-// round(f 2^22) by the exact two-integer split
-__device__ __forceinline__ long long fx_round(float f)
-{
-    unsigned h = 0, l = 0;
-    fx_acc(f, h, l);
-    return (long long)(int)h * 4194304LL + (long long)(int)l;
-}
 
 // a4 + a5: forces on every particle of a tile from its Verlet list, with
 // the neighbour positions read from the tile's halo in shared memory, then
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             double Fd[3] = {0.0, 0.0, 0.0};
             double fscale = 1.0;
             if (PREC == 1) {
-                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 0};
                 if (lstaged) {
                     const unsigned short *nbs = lst + (i - tl.s0);
                     if (R.cubic) neighbours32<ENERGY, true, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
@@ -509,8 +516,9 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                     Fd[k] = ll_to_double((long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k]);
                 fscale = kFixInv;
                 if (ENERGY) {
-                    uf += (long long)(int)a.hu * 4194304LL + (long long)(int)a.lu;
-                    wf += (long long)(int)a.hw * 4194304LL + (long long)(int)a.lw;
+                    // twice this particle's pair energy and virial, in FP32, to fixed point
+                    uf += fx_round(R.eps4_f * a.su - R.vshift_f * (float)a.nin);
+                    wf += fx_round(R.eps24_f * a.sg);
                 }
             } else {
                 const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];

@@ -384,10 +384,13 @@ md_status md_create(const md_params *p, md_handle **out)
         // bands around the cutoffs inside which the FP32 r^2 cannot decide:
         // fixed-point quantisation (|dd| <= sqrt(3) L / 2^32) plus FP32 rounding
         const double qd = std::sqrt(3.0) * Lmax / 4294967296.0;
-        const double brc = 2.0 * rc * qd + std::ldexp(1.0, -16) * rc * rc;
+        // FP32 r^2 from exact integer differences: one rounding per component
+        // and three in the sum of squares, below 5 x 2^-24 relative; 2^-20
+        // leaves a factor of three
+        const double brc = 2.0 * rc * qd + std::ldexp(1.0, -20) * rc * rc;
         // the list walk rounds coordinates relative to the tile centre (|c| <= L / 2)
         // to FP32: up to L / 2^24 more per separation component
-        const double brl = 2.0 * rl * (qd + std::sqrt(3.0) * Lmax / 16777216.0) + std::ldexp(1.0, -16) * rl * rl;
+        const double brl = 2.0 * rl * (qd + std::sqrt(3.0) * Lmax / 16777216.0) + std::ldexp(1.0, -20) * rl * rl;
         R.rc2_lo = (float)(rc * rc - brc);
         R.rc2_hi = (float)(rc * rc + brc);
         R.rl2_lo = (float)(rl * rl - brl);
