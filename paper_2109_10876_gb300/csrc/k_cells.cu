@@ -513,52 +513,54 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_tile_pieces(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
     const int lane = threadIdx.x & 31;
-    const int t = blockIdx.x * kTileWarps + (threadIdx.x >> 5);
-    if (t >= b.ctl->ntiles) return;
-    const Tile tl = b.tiles[t];
-    const Replica &R = b.rep[tl.rep];
-    const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
-    int ly, cntY, lz, cntZ;
-    axis_offsets(ny, ly, cntY);
-    axis_offsets(nz, lz, cntZ);
-    const int nrow = cntY * cntZ;
-    int npc = 0, cnt[2] = {0, 0}, ra[2] = {0, 0}, rb[2] = {0, 0}, s0[2] = {0, 0};
-    if (lane < nrow) {
-        const int oz = lane / cntY, oy = lane - oz * cntY;
-        const int zz = wrapi(tl.cz + lz + oz, nz), yy = wrapi(tl.cy + ly + oy, ny);
-        const int base = R.cell_off + (zz * ny + yy) * nx;
-        const int x0 = tl.x0, x1 = tl.x1;
-        if (x1 - x0 + 2 >= nx) { ra[0] = 0; rb[0] = nx; npc = 1; }
-        else if (x0 == 0) { ra[0] = nx - 1; rb[0] = nx; ra[1] = 0; rb[1] = x1 + 1; npc = 2; }
-        else if (x1 == nx) { ra[0] = x0 - 1; rb[0] = nx; ra[1] = 0; rb[1] = 1; npc = 2; }
-        else { ra[0] = x0 - 1; rb[0] = x1 + 1; npc = 1; }
-        for (int q = 0; q < npc; ++q) {
-            s0[q] = b.cell_start[base + ra[q]];
-            cnt[q] = b.cell_end[base + rb[q] - 1] - s0[q];
+    const int nt = b.ctl->ntiles;
+    // a bounded grid walks the tiles (their count is known on the device only)
+    for (int t = blockIdx.x * kTileWarps + (threadIdx.x >> 5); t < nt; t += gridDim.x * kTileWarps) {
+        const Tile tl = b.tiles[t];
+        const Replica &R = b.rep[tl.rep];
+        const int nx = R.ncell[0], ny = R.ncell[1], nz = R.ncell[2];
+        int ly, cntY, lz, cntZ;
+        axis_offsets(ny, ly, cntY);
+        axis_offsets(nz, lz, cntZ);
+        const int nrow = cntY * cntZ;
+        int npc = 0, cnt[2] = {0, 0}, ra[2] = {0, 0}, rb[2] = {0, 0}, s0[2] = {0, 0};
+        if (lane < nrow) {
+            const int oz = lane / cntY, oy = lane - oz * cntY;
+            const int zz = wrapi(tl.cz + lz + oz, nz), yy = wrapi(tl.cy + ly + oy, ny);
+            const int base = R.cell_off + (zz * ny + yy) * nx;
+            const int x0 = tl.x0, x1 = tl.x1;
+            if (x1 - x0 + 2 >= nx) { ra[0] = 0; rb[0] = nx; npc = 1; }
+            else if (x0 == 0) { ra[0] = nx - 1; rb[0] = nx; ra[1] = 0; rb[1] = x1 + 1; npc = 2; }
+            else if (x1 == nx) { ra[0] = x0 - 1; rb[0] = nx; ra[1] = 0; rb[1] = 1; npc = 2; }
+            else { ra[0] = x0 - 1; rb[0] = x1 + 1; npc = 1; }
+            for (int q = 0; q < npc; ++q) {
+                s0[q] = b.cell_start[base + ra[q]];
+                cnt[q] = b.cell_end[base + rb[q] - 1] - s0[q];
+            }
         }
-    }
-    // exclusive prefix over lanes of pieces and halo sizes
-    int pinc = npc, hinc = cnt[0] + cnt[1];
-    for (int o = 1; o < 32; o <<= 1) {
-        const int a = __shfl_up_sync(0xffffffffu, pinc, o), c = __shfl_up_sync(0xffffffffu, hinc, o);
-        if (lane >= o) { pinc += a; hinc += c; }
-    }
-    const int pbase = pinc - npc, hbase = hinc - (cnt[0] + cnt[1]);
-    Piece *out = b.pieces + (size_t)t * (kMaxPieces + 1);
-    int h = hbase;
-    for (int q = 0; q < npc; ++q) {
-        Piece pq;
-        pq.row = lane; pq.xa = ra[q]; pq.xb = rb[q]; pq.slot0 = s0[q]; pq.hoff = h; pq.n = cnt[q];
-        out[pbase + q] = pq;
-        h += cnt[q];
-    }
-    const int np = __shfl_sync(0xffffffffu, pinc, 31), H = __shfl_sync(0xffffffffu, hinc, 31);
-    if (lane == 0) {
-        Piece last;
-        last.row = nrow; last.xa = last.xb = 0; last.slot0 = 0; last.hoff = H; last.n = 0;
-        out[np] = last;
-        b.tile_np[t] = np;
-        atomicMax(&b.ctl->max_halo, H);
+        // exclusive prefix over lanes of pieces and halo sizes
+        int pinc = npc, hinc = cnt[0] + cnt[1];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, pinc, o), c = __shfl_up_sync(0xffffffffu, hinc, o);
+            if (lane >= o) { pinc += a; hinc += c; }
+        }
+        const int pbase = pinc - npc, hbase = hinc - (cnt[0] + cnt[1]);
+        Piece *out = b.pieces + (size_t)t * (kMaxPieces + 1);
+        int h = hbase;
+        for (int q = 0; q < npc; ++q) {
+            Piece pq;
+            pq.row = lane; pq.xa = ra[q]; pq.xb = rb[q]; pq.slot0 = s0[q]; pq.hoff = h; pq.n = cnt[q];
+            out[pbase + q] = pq;
+            h += cnt[q];
+        }
+        const int np = __shfl_sync(0xffffffffu, pinc, 31), H = __shfl_sync(0xffffffffu, hinc, 31);
+        if (lane == 0) {
+            Piece last;
+            last.row = nrow; last.xa = last.xb = 0; last.slot0 = 0; last.hoff = H; last.n = 0;
+            out[np] = last;
+            b.tile_np[t] = np;
+            atomicMax(&b.ctl->max_halo, H);
+        }
     }
 }
 
@@ -1011,7 +1013,7 @@ void launch_rebuild_chain(const Bufs &b, cudaStream_t st)
     k_tile_count<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
     k_tile_scan<<<1, kScanThreads, 0, st>>>(b);
     k_tile_write<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
-    k_tile_pieces<<<blocks_for(b.C, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
+    k_tile_pieces<<<(unsigned)std::min<long long>(blocks_for(b.C, kTileWarps), 4096), 32 * kTileWarps, 0, st>>>(b);
     const size_t smem = list_smem_bytes(b.hcap);
     k_build_list<<<list_grid(smem), kBlock, smem, st>>>(b);
 }
