@@ -44,6 +44,21 @@ __device__ __forceinline__ void fx_acc2(float a, float c, unsigned &hi, unsigned
     lo += __float_as_uint(t2) - kMagicBits;
 }
 
+// Two neighbours at once with the packed FP32 instructions of this part
+// (each lane of a float2 rounds exactly as the scalar instruction does).  The
+// integer pieces are added without their bias kMagicBits; the caller removes
+// it once per term at the end (all sums are modulo 2^32, so this is exact).
+__device__ __forceinline__ void fx_acc2x2(float2 a, float2 c, unsigned &hi, unsigned &lo)
+{
+    const float2 M = make_float2(kMagic, kMagic);
+    const float2 t1 = __ffma2_rn(a, c, M);                                   // kMagic + round(a c)
+    const float2 nh = __ffma2_rn(t1, make_float2(-1.0f, -1.0f), M);          // -round(a c), exact
+    const float2 r = __ffma2_rn(a, c, nh);                                   // a c - round(a c)
+    const float2 t2 = __ffma2_rn(r, make_float2(kFixScale, kFixScale), M);   // kMagic + round(r 2^22)
+    hi += __float_as_uint(t1.x) + __float_as_uint(t1.y);
+    lo += __float_as_uint(t2.x) + __float_as_uint(t2.y);
+}
+
 // Reciprocal by the hardware approximation (a pure function of its input).
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -343,6 +358,30 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, b
     }
 }
 
+// pair32 for two neighbours (the same arithmetic, packed); the fixed-point
+// pieces carry the bias of fx_acc2x2
+template <bool ENERGY>
+__device__ __forceinline__ void pair32x2(float2 dx, float2 dy, float2 dz, float2 r2, bool in0, bool in1, float sig2,
+                                         float eps24, Acc32 &a)
+{
+    const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    const float2 s2 = __fmul2_rn(make_float2(sig2, sig2), ir2);
+    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+    const float2 g = __fmul2_rn(s6, __ffma2_rn(make_float2(2.0f, 2.0f), s6, make_float2(-1.0f, -1.0f)));
+    float2 fs = __fmul2_rn(__fmul2_rn(make_float2(eps24, eps24), g), ir2);
+    fs.x = in0 ? fs.x : 0.0f;
+    fs.y = in1 ? fs.y : 0.0f;
+    fx_acc2x2(fs, dx, a.hx, a.lx);
+    fx_acc2x2(fs, dy, a.hy, a.ly);
+    fx_acc2x2(fs, dz, a.hz, a.lz);
+    if (ENERGY) {
+        const float2 e = __fmul2_rn(s6, __fadd2_rn(s6, make_float2(-1.0f, -1.0f)));
+        a.su += (in0 ? e.x : 0.0f) + (in1 ? e.y : 0.0f);
+        a.sg += (in0 ? g.x : 0.0f) + (in1 ? g.y : 0.0f);
+        a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+    }
+}
+
 // separation of two fixed-point positions in units u of the x axis
 template <bool CUBIC>
 __device__ __forceinline__ void sep_u(uint4 a, uint4 c, float ry, float rz, float &dx, float &dy, float &dz, float &r2)
@@ -351,7 +390,8 @@ __device__ __forceinline__ void sep_u(uint4 a, uint4 c, float ry, float rz, floa
     dy = (float)(int)(a.y - c.y);
     dz = (float)(int)(a.z - c.z);
     if (!CUBIC) { dy *= ry; dz *= rz; }
-    r2 = dx * dx + dy * dy + dz * dz;
+    // the rounding order of the packed loop, so that both see the same r^2
+    r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
 // FP32 neighbour loop of one particle: padded list, branch-free arithmetic;
@@ -371,15 +411,28 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
 #pragma unroll
         for (int u = 0; u < kU; ++u) hh[u] = LSMEM ? nb[(k0 + u) * Pt] : __ldg(nb + (long long)(k0 + u) * Pt);
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            float dx, dy, dz, r2;
-            sep_u<CUBIC>(pi, hpos[hh[u]], ry, rz, dx, dy, dz, r2);
-            const bool nz = r2 > 0.0f;              // padding entries are the particle itself
-            const bool in = (r2 < lo) & nz;
-            nband += (r2 < hi) & !(r2 < lo);
-            tooclose |= (r2 < fmax2) & nz;
-            pair32<ENERGY>(dx, dy, dz, r2, in, sig2, eps24, a);
+        for (int u = 0; u < kU; u += 2) {
+            const uint4 q0 = hpos[hh[u]], q1 = hpos[hh[u + 1]];
+            float2 dx = make_float2((float)(int)(pi.x - q0.x), (float)(int)(pi.x - q1.x));
+            float2 dy = make_float2((float)(int)(pi.y - q0.y), (float)(int)(pi.y - q1.y));
+            float2 dz = make_float2((float)(int)(pi.z - q0.z), (float)(int)(pi.z - q1.z));
+            if (!CUBIC) {
+                dy = __fmul2_rn(dy, make_float2(ry, ry));
+                dz = __fmul2_rn(dz, make_float2(rz, rz));
+            }
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            // padding entries are the particle itself (r^2 = 0)
+            const bool nz0 = r2.x > 0.0f, nz1 = r2.y > 0.0f;
+            const bool in0 = (r2.x < lo) & nz0, in1 = (r2.y < lo) & nz1;
+            nband += ((r2.x < hi) & !(r2.x < lo)) + ((r2.y < hi) & !(r2.y < lo));
+            tooclose |= ((r2.x < fmax2) & nz0) | ((r2.y < fmax2) & nz1);
+            pair32x2<ENERGY>(dx, dy, dz, r2, in0, in1, sig2, eps24, a);
         }
+    }
+    {
+        // remove the bias of the npad packed terms of every accumulator
+        const unsigned bias = (unsigned)npad * kMagicBits;
+        a.hx -= bias; a.lx -= bias; a.hy -= bias; a.ly -= bias; a.hz -= bias; a.lz -= bias;
     }
     if (nband) {
         // pairs within rounding of r_cut: membership decided in FP64 from the
