@@ -206,25 +206,32 @@ __global__ void k_set_steps(Ctl *ctl, long long left)
 }
 
 // ---------------------------------------------------------------- counting sort
-// a1: cell id of every particle and the cell histogram.
+// a1: cell id of every particle and the cell histogram.  Slots are still in
+// the previous build's cell order, so the lanes of a warp mostly share a few
+// cells: one atomic per distinct cell of the warp (its lanes found by a match).
 __global__ void k_bin(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
+    const unsigned full = 0xffffffffu;
+    if (__shfl_sync(full, (int)(!b.ctl->rebuild || b.ctl->err), 0)) return;   // warp-uniform
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         b.ctl->max_nn = 0;
         b.ctl->list_entries = 0;
         b.ctl->max_occ = 0;
     }
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.S) return;
-    uint4 p = b.pos[b.ctl->cur][s];
-    if ((int)p.w < 0) return;
-    const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
-    int cx, cy, cz;
-    cell_coords(p, R, cx, cy, cz);
-    int c = R.cell_off + (cz * R.ncell[1] + cy) * R.ncell[0] + cx;
-    b.cellid[s] = c;
-    atomicAdd(&b.cell_count[c], 1);
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int c = -1;
+    if (s < b.S) {
+        const uint4 p = b.pos[b.ctl->cur][s];
+        if ((int)p.w >= 0) {
+            const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
+            int cx, cy, cz;
+            cell_coords(p, R, cx, cy, cz);
+            c = R.cell_off + (cz * R.ncell[1] + cy) * R.ncell[0] + cx;
+            b.cellid[s] = c;
+        }
+    }
+    const unsigned peers = __match_any_sync(full, c);
+    if (c >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&b.cell_count[c], __popc(peers));
 }
 
 constexpr int kScanThreads = 1024;
@@ -308,16 +315,22 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_write(Bufs b)
 }
 
 // Scatter each particle's old slot into its cell's bucket (order within a
-// cell is fixed afterwards by k_reorder).
+// cell is fixed afterwards by k_reorder): one atomic per distinct cell of the
+// warp, its lanes taking consecutive places.
 __global__ void k_scatter(Bufs b)
 {
-    if (!b.ctl->rebuild || b.ctl->err) return;
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.S) return;
-    if ((int)b.pos[b.ctl->cur][s].w < 0) return;
-    int c = b.cellid[s];
-    int k = atomicAdd(&b.cell_end[c], 1);
-    b.bucket[k] = (int)s;
+    const unsigned full = 0xffffffffu;
+    if (__shfl_sync(full, (int)(!b.ctl->rebuild || b.ctl->err), 0)) return;   // warp-uniform
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int c = -1;
+    if (s < b.S && (int)b.pos[b.ctl->cur][s].w >= 0) c = b.cellid[s];
+    const unsigned peers = __match_any_sync(full, c);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (c >= 0 && lane == leader) base = atomicAdd(&b.cell_end[c], __popc(peers));
+    base = __shfl_sync(full, base, leader);
+    if (c >= 0) b.bucket[base + __popc(peers & ((1u << lane) - 1u))] = (int)s;
 }
 
 // One warp per cell: order the cell's members by (fixed-point x, particle
