@@ -553,6 +553,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));   // entry k at nb[k Pt]
             double Fd[3] = {0.0, 0.0, 0.0};
             double fscale = 1.0;
+            double ckick = b.half_dt_over_m;     // half kick per unit of Fd
             if (PREC == 1) {
                 Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 0};
                 if (lstaged) {
@@ -568,6 +569,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 for (int k = 0; k < 3; ++k)
                     Fd[k] = ll_to_double((long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k]);
                 fscale = kFixInv;
+                ckick = b.half_dt_over_m_fix;
                 if (ENERGY) {
                     // twice this particle's pair energy and virial, in FP32, to fixed point
                     uf += fx_round(R.eps4_f * a.su - R.vshift_f * (float)a.nin);
@@ -709,6 +711,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 if (b.langevin) {
                     for (int k = 0; k < 3; ++k) Fd[k] *= fscale;
                     fscale = 1.0;
+                    ckick = b.half_dt_over_m;
                     langevin(b, (int)pi.w, step, v, Fd);
                 }
             }
@@ -730,7 +733,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                     else ki += 0.5 * b.mass * w2;
                 }
             } else if (MODE == kModeFinal) {
-                const double c = b.half_dt_over_m * fscale;
+                const double c = ckick;
                 for (int k = 0; k < 3; ++k) {
                     v[k] += c * Fd[k];
                     b.v[cur][k * b.S + i] = v[k];
@@ -742,7 +745,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                     else ki += 0.5 * b.mass * w2;
                 }
             } else {  // kModeFused: end of step n, then the first half kick and drift of step n + 1
-                const double c = b.half_dt_over_m * fscale;
+                const double c = ckick;
                 double xi[3];
                 for (int k = 0; k < 3; ++k) v[k] += c * Fd[k];
                 if (ENERGY) {

@@ -493,6 +493,7 @@ md_status md_create(const md_params *p, md_handle **out)
     b.dt = p->dt;
     b.mass = p->mass;
     b.half_dt_over_m = 0.5 * p->dt / p->mass;
+    b.half_dt_over_m_fix = std::ldexp(b.half_dt_over_m, -22);
     b.gamma = p->langevin_gamma;
     b.kT = p->kT;
     b.langevin = p->langevin_gamma > 0 ? 1 : 0;

@@ -214,6 +214,7 @@ struct Bufs {
     int has_bonds;
     int langevin;
     double dt, mass, half_dt_over_m;
+    double half_dt_over_m_fix;   // half_dt_over_m * 2^-22 (exact): the kick factor of fixed-point forces
     double gamma, kT, noise_amp;  // noise_amp = sqrt(24 gamma kT m / dt)
     double fene_K, fene_R02;
     float fene_K_f, fene_R02_f;
