@@ -39,6 +39,10 @@ RHO, T0, RC, SKIN, DT = 0.8442, 0.72, 2.5, 0.3, 0.005
 # besides the list: own fixed-point position 16, list length 4, x read+write 48,
 # v read+write 48, new fixed-point position 16, build-time position 16
 FORCE_FIXED_BYTES = 16 + 4 + 48 + 48 + 16 + 16
+# the half list adds, per particle, the fixed-point force sums: 24 B written
+# by the pair pass (the atomics' net result), 24 B read and 24 B cleared by
+# the integrating pass
+HALF_SUM_BYTES = 3 * 24
 # kernels of one list rebuild: bin, 3-phase scan, scatter, reorder, tile count /
 # scan / write / pieces, list build
 REBUILD_KERNELS = 11
@@ -54,6 +58,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64, CPU baseline and force error")
     ap.add_argument("--workload", default="lj", choices=["lj", "melt", "rings", "slab", "sphere"],
                     help="lj: the LJ fluid line (default); melt / rings / slab / sphere: one line for that workload")
+    ap.add_argument("--list", default="full", choices=["full", "half"],
+                    help="Verlet-list form of the timed LJ-fluid run: full (default; every pair from both ends) "
+                         "or half (Newton's third law, partner shares by 64-bit atomics)")
     return ap.parse_args()
 
 
@@ -469,6 +476,9 @@ def main():
 
     # ---- device-resident timed run (FP32 pair math + fixed-point sums)
     h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+    half = args.list == "half"
+    if half:
+        md.md_set_half_list(h, True)
     md.md_set_state(h, xt, vt)
     md.md_build_neighbors(h)
     tile_size = md.md_autotune(h, 10)     # tile size by timed trial steps (state restored)
@@ -502,15 +512,18 @@ def main():
     mean_nn = st1["list_entries"] / n
     pad = 4
     list_bytes = 2.0 * (mean_nn + (pad - 1) / 2.0)
-    bytes_pp = FORCE_FIXED_BYTES + list_bytes
+    bytes_pp = FORCE_FIXED_BYTES + list_bytes + (HALF_SUM_BYTES if half else 0)
+    # the force section holds one fused launch per step (two with the half list)
     force_ms = sect_ms[md.MD_SECT_FORCE] / max(sect_n[md.MD_SECT_FORCE], 1)
     achieved = n * bytes_pp / (force_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     digest = csrc_digest()
     tpp = profiled_traffic(digest)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None if tpp is None else round(tpp * n),
-                "peak_source": peak_kind, "kernel": "k_force<FP32, fused>",
+                "frac": round(achieved / peak, 4),
+                "traffic": None if (tpp is None or half) else round(tpp * n),
+                "peak_source": peak_kind,
+                "kernel": "k_pairs_half + k_force<FP32, fused, half>" if half else "k_force<FP32, fused>",
                 "algorithmic_bytes_per_particle": round(bytes_pp, 1),
                 "launch_ms": round(force_ms, 4)}
 
@@ -567,6 +580,35 @@ def main():
         extras["fp64"] = {"value": world * v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
                           "speedup_fp32_fixed_over_fp64": (value / world) / v64}
 
+        # ---- the other list form on the same input (Sec. 2.1.2: the half list
+        # of Newton's third law against the full list)
+        kh = max(20, min(args.steps, 200))
+        h5 = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+        md.md_set_tile_size(h5, tile_size)
+        md.md_set_half_list(h5, not half)
+        md.md_set_state(h5, xt, vt)
+        md.md_build_neighbors(h5)
+        md.md_step(h5, 3)
+        md.md_sync(h5)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        md.md_step(h5, kh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msh = e0.elapsed_time(e1)
+        md.md_set_timing(h5, True)
+        md.md_step(h5, kh)
+        sms, sn = md.md_get_timing(h5)
+        h5.destroy()
+        vh_ = n * kh / (msh * 1e-3)
+        extras["half_list" if not half else "full_list"] = {
+            "value": world * vh_, "unit": UNIT, "ms_per_step": msh / kh, "steps": kh,
+            "force_ms_per_step": sms[md.MD_SECT_FORCE] / max(sn[md.MD_SECT_FORCE], 1),
+            "neigh_ms_per_step": sms[md.MD_SECT_NEIGH] / kh,
+            "ratio_to_timed_run": vh_ / (value / world),
+            "note": "graph-launched steps on the same input; force_ms_per_step from a second pass "
+                    "with per-launch events (the half list's force step is two kernels)"}
+
         extras["ensemble"] = ensemble_leg(md, torch, dev)
 
         if world == 1 and rank == 0:
@@ -597,12 +639,14 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": f"LJ fluid N={n} per GPU (fcc {args.ncell}^3 x 4), rho={RHO}, T*={T0}, "
                                        f"rc={RC} shifted, skin={SKIN}, dt={DT}, NVE, FP32 pairs + 64-bit fixed-point "
-                                       f"sums", "particles_per_gpu": n, "tile_size": tile_size,
+                                       f"sums, {args.list} Verlet list", "particles_per_gpu": n,
+                           "tile_size": tile_size,
                            "parallelism": "replicas only" if world > 1 else "1 GPU",
                            "l2": "working set larger than L2 (positions, velocities and the Verlet list: "
                                  f"~{(n * (FORCE_FIXED_BYTES + list_bytes)) / 1e6:.0f} MB touched per step)"},
                 "roofline": roofline,
-                "gpu_launches": 2 * args.steps + 3 + REBUILD_KERNELS * (st1["rebuilds"] - st0["rebuilds"]),
+                "gpu_launches": (3 if half else 2) * args.steps + 3 +
+                                REBUILD_KERNELS * (st1["rebuilds"] - st0["rebuilds"]),
                 "rebuilds": st1["rebuilds"] - st0["rebuilds"],
                 "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / args.steps,
                                          "force_integrate": sect_ms[md.MD_SECT_FORCE] / args.steps,

@@ -203,6 +203,24 @@ md_status md_autotune(md_handle *h, int32_t trial_steps, int32_t *tile_max_out, 
  * MD_ERR_ARG outside 1..128. */
 md_status md_set_tile_size(md_handle *h, int32_t tile_size, void *stream);
 
+/* Choose the Verlet-list form (Sec. 2.1.2): enable = 0 (the default) keeps
+ * the full list, in which every pair is stored and evaluated from both of its
+ * particles; enable = 1 switches to the half list of Newton's third law, in
+ * which each pair is stored once (in the list of the particle that comes
+ * first in the cell order) and its force is added to one particle and
+ * subtracted from the other.  The partner's share goes through 64-bit integer
+ * atomic adds into fixed-point force sums of 3 x (slots) int64 that the
+ * handle allocates on the first enable and keeps until md_destroy; the
+ * integration then runs as a second kernel.  Both forms give bit-identical
+ * forces and trajectories: every pair force is rounded to the fixed point the
+ * same way whichever end evaluates it, and the sums are exact.  Energies and
+ * virials agree to FP32 rounding.  The next step, force or list call rebuilds
+ * the list on `stream`.  MD_ERR_ARG for enable = 1 with MD_FP64, with FENE
+ * bonds or angle triples; md_forward / md_backward need the full list and
+ * return MD_ERR_ARG while the half list is on.  MD_ERR_CUDA if the sums cannot
+ * be allocated. */
+md_status md_set_half_list(md_handle *h, int32_t enable, void *stream);
+
 /* Wait for all work on `stream` and return any latched device error. */
 md_status md_sync(md_handle *h, void *stream);
 

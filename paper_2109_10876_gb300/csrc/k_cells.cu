@@ -710,7 +710,11 @@ __device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, con
 // next free row and the row pointer advances only on a hit.  The shared stage
 // has the final [row][particle] layout of the tile's list block; a list that
 // outgrows it is walked again straight into global memory (rare).
-template <bool REL>
+// HALF: the half list of Newton's third law (Sec. 2.1.2), each pair once, in
+// the list of the particle with the lower slot: candidate h of range r has
+// slot j0 + (h - h0), so it is kept only when h > i - j0 + h0.  Every pair of
+// the full list survives in exactly one of its two lists (slots are unique).
+template <bool REL, bool HALF>
 __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, const Tile &tl, const Piece *pc, int np,
                                               const typename Cand<REL>::T *halo, unsigned short *lst, const double *X,
                                               int hfirst, int (*rng)[kMaxPieces][3], int *s_kmax, int &mx,
@@ -754,6 +758,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         for (int r = 0; r < nrng; ++r) {
             const int h1 = rng[half][r][1];
             int h = rng[half][r][0];
+            const int thr = HALF ? i - rng[half][r][2] + h : 0;   // HALF: keep halo indices above thr
             for (; h + 4 <= h1; h += 4) {
                 T pj[4];
 #pragma unroll
@@ -763,7 +768,8 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const float r2 = C::sep2(p, pj[u], ry, rz);
-                    const bool in = (r2 < lo) & (C::index(pj[u], h + u) != self);
+                    const int hj = C::index(pj[u], h + u);
+                    const bool in = (r2 < lo) & (HALF ? hj > thr : hj != self);
                     tie |= (r2 < hi) & !(r2 < lo);
                     *q = (unsigned short)C::index(pj[u], h + u);
                     q += in ? stride : 0;
@@ -772,7 +778,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             }
             for (; h < h1; ++h) {
                 const float r2 = C::sep2(p, halo[h], ry, rz);
-                const bool in = (r2 < lo) & (h != self);
+                const bool in = (r2 < lo) & (HALF ? h > thr : h != self);
                 tie |= (r2 < hi) & !(r2 < lo);
                 col[max(min(cnt, cap - 4), 0) * stride] = (unsigned short)h;
                 cnt += in;
@@ -782,9 +788,11 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         if (tie && valid) {
             for (int r = 0; r < nrng; ++r) {
                 const int h0 = rng[half][r][0], h1 = rng[half][r][1], j0 = rng[half][r][2];
+                const int thr = HALF ? i - j0 + h0 : 0;
                 for (int h = h0; h < h1; ++h) {
                     const float r2 = C::sep2(p, halo[h], ry, rz);
-                    if ((r2 < hi) & !(r2 < lo) & (h != self) && r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2) {
+                    if ((r2 < hi) & !(r2 < lo) & (HALF ? h > thr : h != self) &&
+                        r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2) {
                         col[max(min(cnt, cap - 1), 0) * stride] = (unsigned short)h;
                         ++cnt;
                     }
@@ -801,17 +809,21 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 else if (c2 < b.K) b.nbr[nbr_index(tl.s0, Pt, b.K, c2, pp)] = (unsigned short)h;
                 ++c2;
             };
-            for (int r = 0; r < nrng; ++r)
+            for (int r = 0; r < nrng; ++r) {
+                const int thr = HALF ? i - rng[half][r][2] + rng[half][r][0] : 0;
                 for (int h = rng[half][r][0]; h < rng[half][r][1]; ++h) {
                     const float r2 = C::sep2(p, halo[h], ry, rz);
-                    if ((r2 < lo) & (h != self)) put(h);
+                    if ((r2 < lo) & (HALF ? h > thr : h != self)) put(h);
                 }
+            }
             if (tie)
                 for (int r = 0; r < nrng; ++r) {
                     const int h0 = rng[half][r][0], h1 = rng[half][r][1], j0 = rng[half][r][2];
+                    const int thr = HALF ? i - j0 + h0 : 0;
                     for (int h = h0; h < h1; ++h) {
                         const float r2 = C::sep2(p, halo[h], ry, rz);
-                        if ((r2 < hi) & !(r2 < lo) & (h != self) && r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2)
+                        if ((r2 < hi) & !(r2 < lo) & (HALF ? h > thr : h != self) &&
+                            r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2)
                             put(h);
                     }
                 }
@@ -889,8 +901,13 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
         }
         __syncthreads();
         const int hfirst = tile_self_offset(R, tl, pc, s_np);
-        if (rel) cells_of_tile<true>(b, R, tl, pc, s_np, halof, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
-        else cells_of_tile<false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
+        if (b.half_list) {
+            if (rel) cells_of_tile<true, true>(b, R, tl, pc, s_np, halof, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
+            else cells_of_tile<false, true>(b, R, tl, pc, s_np, halo, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
+        } else {
+            if (rel) cells_of_tile<true, false>(b, R, tl, pc, s_np, halof, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
+            else cells_of_tile<false, false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
+        }
         __syncthreads();
         if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;
         // the staged rows are the start of the tile's list block: one
@@ -955,9 +972,11 @@ __global__ void k_export_pairs(Bufs b, int *pairs, long long cap, unsigned long 
                 while (q + 1 < s_np && h >= pc[q + 1].hoff) ++q;
                 const int j = pc[q].slot0 + (h - pc[q].hoff);
                 const int idj = (int)P[j].w;
-                if (idi < idj) {
+                // a full list holds every pair twice (kept once, from its
+                // lower id), a half list once (exported as (lower, higher))
+                if (b.half_list || idi < idj) {
                     unsigned long long w = atomicAdd(count, 1ull);
-                    if ((long long)w < cap) { pairs[2 * w] = idi; pairs[2 * w + 1] = idj; }
+                    if ((long long)w < cap) { pairs[2 * w] = min(idi, idj); pairs[2 * w + 1] = max(idi, idj); }
                 }
             }
         }

@@ -448,6 +448,141 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
     if (tooclose) err |= kErrFixed;
 }
 
+// ---------------------------------------------------------------- half list
+// Newton's third law (Sec. 2.1.2): a half list holds each pair once, and the
+// pair force goes to both particles.  The two exactly rounded pieces of each
+// component are those of fx_acc2 / fx_acc2x2, so round(f_ij 2^22) is the
+// same integer whichever end evaluates the pair, and its negation is
+// round(f_ji 2^22) (the rounding is odd): the half-list forces are the
+// full-list forces bit for bit.
+
+// round(a c 2^22) of one lane as a 64-bit fixed-point value, from the biased
+// pieces t1 = kMagic + round(a c), t2 = kMagic + round(r 2^22)
+__device__ __forceinline__ long long fx_value(float t1, float t2)
+{
+    return (long long)(int)(__float_as_uint(t1) - kMagicBits) * 4194304LL +
+           (long long)(int)(__float_as_uint(t2) - kMagicBits);
+}
+
+// fx_acc2x2 that also returns both lanes' values
+__device__ __forceinline__ void fx_acc2x2_v(float2 a, float2 c, unsigned &hi, unsigned &lo, long long &v0,
+                                            long long &v1)
+{
+    const float2 M = make_float2(kMagic, kMagic);
+    const float2 t1 = __ffma2_rn(a, c, M);
+    const float2 nh = __ffma2_rn(t1, make_float2(-1.0f, -1.0f), M);
+    const float2 r = __ffma2_rn(a, c, nh);
+    const float2 t2 = __ffma2_rn(r, make_float2(kFixScale, kFixScale), M);
+    hi += __float_as_uint(t1.x) + __float_as_uint(t1.y);
+    lo += __float_as_uint(t2.x) + __float_as_uint(t2.y);
+    v0 = fx_value(t1.x, t2.x);
+    v1 = fx_value(t1.y, t2.y);
+}
+
+// the scalar value of fx_acc2 (same instructions, same rounding)
+__device__ __forceinline__ long long fx_value1(float a, float c)
+{
+    const float t1 = __fmaf_rn(a, c, kMagic);
+    const float h = __fsub_rn(t1, kMagic);
+    const float r = __fmaf_rn(a, c, -h);
+    const float t2 = __fmaf_rn(r, kFixScale, kMagic);
+    return fx_value(t1, t2);
+}
+
+// subtract v from the fixed-point sum at *p (the reaction on the partner)
+__device__ __forceinline__ void red_sub(long long *p, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)(-v));
+}
+
+// pair32x2 for the half list: the same arithmetic, plus the reactions of
+// both neighbours (slots s0, s1) into the global fixed-point sums
+template <bool ENERGY>
+__device__ __forceinline__ void pair32x2_half(float2 dx, float2 dy, float2 dz, float2 r2, bool in0, bool in1,
+                                              float sig2, float eps24, Acc32 &a, long long *Fq, long long S,
+                                              unsigned s0, unsigned s1)
+{
+    const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    const float2 s2 = __fmul2_rn(make_float2(sig2, sig2), ir2);
+    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+    const float2 g = __fmul2_rn(s6, __ffma2_rn(make_float2(2.0f, 2.0f), s6, make_float2(-1.0f, -1.0f)));
+    float2 fs = __fmul2_rn(__fmul2_rn(make_float2(eps24, eps24), g), ir2);
+    fs.x = in0 ? fs.x : 0.0f;
+    fs.y = in1 ? fs.y : 0.0f;
+    long long x0, x1, y0, y1, z0, z1;
+    fx_acc2x2_v(fs, dx, a.hx, a.lx, x0, x1);
+    fx_acc2x2_v(fs, dy, a.hy, a.ly, y0, y1);
+    fx_acc2x2_v(fs, dz, a.hz, a.lz, z0, z1);
+    if (in0) { red_sub(Fq + s0, x0); red_sub(Fq + S + s0, y0); red_sub(Fq + 2 * S + s0, z0); }
+    if (in1) { red_sub(Fq + s1, x1); red_sub(Fq + S + s1, y1); red_sub(Fq + 2 * S + s1, z1); }
+    if (ENERGY) {
+        const float2 e = __fmul2_rn(s6, __fadd2_rn(s6, make_float2(-1.0f, -1.0f)));
+        a.su += (in0 ? e.x : 0.0f) + (in1 ? e.y : 0.0f);
+        a.sg += (in0 ? g.x : 0.0f) + (in1 ? g.y : 0.0f);
+        a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+    }
+}
+
+// neighbours32 over a half list: the staged halo carries each particle's slot
+// in .w, where the reactions go
+template <bool ENERGY, bool CUBIC>
+__device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 *hpos, const unsigned short *nb, int Pt,
+                                                  int n, int npad, uint4 pi, const double *X, long long S, long long i,
+                                                  const Piece *pc, int np, Acc32 &a, int &err, long long *Fq)
+{
+    const float ry = R.ry, rz = R.rz;
+    const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
+    const float sig2 = R.sig2_u, eps24 = R.eps24_u;
+    int nband = 0;
+    bool tooclose = false;
+    for (int k0 = 0; k0 < npad; k0 += kU) {
+        int hh[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) hh[u] = nb[(k0 + u) * Pt];
+#pragma unroll
+        for (int u = 0; u < kU; u += 2) {
+            const uint4 q0 = hpos[hh[u]], q1 = hpos[hh[u + 1]];
+            float2 dx = make_float2((float)(int)(pi.x - q0.x), (float)(int)(pi.x - q1.x));
+            float2 dy = make_float2((float)(int)(pi.y - q0.y), (float)(int)(pi.y - q1.y));
+            float2 dz = make_float2((float)(int)(pi.z - q0.z), (float)(int)(pi.z - q1.z));
+            if (!CUBIC) {
+                dy = __fmul2_rn(dy, make_float2(ry, ry));
+                dz = __fmul2_rn(dz, make_float2(rz, rz));
+            }
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const bool nz0 = r2.x > 0.0f, nz1 = r2.y > 0.0f;
+            const bool in0 = (r2.x < lo) & nz0, in1 = (r2.y < lo) & nz1;
+            nband += ((r2.x < hi) & !(r2.x < lo)) + ((r2.y < hi) & !(r2.y < lo));
+            tooclose |= ((r2.x < fmax2) & nz0) | ((r2.y < fmax2) & nz1);
+            pair32x2_half<ENERGY>(dx, dy, dz, r2, in0, in1, sig2, eps24, a, Fq, S, q0.w, q1.w);
+        }
+    }
+    {
+        const unsigned bias = (unsigned)npad * kMagicBits;
+        a.hx -= bias; a.lx -= bias; a.hy -= bias; a.ly -= bias; a.hz -= bias; a.lz -= bias;
+    }
+    if (nband) {
+        for (int k = 0; k < n; ++k) {
+            const int h = nb[k * Pt];
+            const uint4 q = hpos[h];
+            float dx, dy, dz, r2;
+            sep_u<CUBIC>(pi, q, ry, rz, dx, dy, dz, r2);
+            if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, (long long)q.w, R.L) < R.rc2) {
+                pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, a);
+                // the force scalar of pair32, for the partner's share
+                const float ir2 = rcp_approx(r2);
+                const float s2 = sig2 * ir2;
+                const float s6 = s2 * s2 * s2;
+                const float fs = eps24 * (s6 * (2.0f * s6 - 1.0f)) * ir2;
+                red_sub(Fq + q.w, fx_value1(fs, dx));
+                red_sub(Fq + S + q.w, fx_value1(fs, dy));
+                red_sub(Fq + 2 * S + q.w, fx_value1(fs, dz));
+            }
+        }
+    }
+    if (tooclose) err |= kErrFixed;
+}
+
 // Cosine angle term K (1 - cos theta) of a triple (a, b, c) with bond vectors
 // b1 = x_b - x_a, b2 = x_c - x_b and c = b1.b2 / (|b1| |b2|): the force on the
 // particle of the given role, F_a = -K (b2/(l1 l2) - c b1/l1^2),
@@ -472,7 +607,11 @@ __device__ __forceinline__ void angle_term(const Real b1[3], const Real b2[3], R
 // the neighbour positions read from the tile's halo in shared memory, then
 // the velocity-Verlet update of that particle.  Persistent blocks take tiles
 // from a work counter.
-template <int PREC, int MODE, bool ENERGY>
+// HALF (FP32 only): the second kernel of a half-list step.  k_pairs_half has
+// left each particle's total pair force in the fixed-point sums Fq; this pass
+// takes it from there (and clears it) instead of walking a list, then does
+// exactly what the full-list kernel does with the force.
+template <int PREC, int MODE, bool ENERGY, bool HALF = false>
 __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) k_force(Bufs b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -508,35 +647,37 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         const Replica &R = b.rep[tl.rep];
         const int np = s_np;
         const int Pt = tl.s1 - tl.s0;
-        if (pc[np].hoff > b.hcap) {          // the list build rejects such tiles first
+        if (!HALF && pc[np].hoff > b.hcap) {          // the list build rejects such tiles first
             err |= kErrList;
             if (threadIdx.x == 0) s_tile = t_next;
             __syncthreads();
             continue;
         }
         const bool own_staged = Pt <= kTileMax;
-        if (own_staged)
-            for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
-        if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
-        if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
-        else stage_halo<double>(pc, np, [&](int h, int j) {
-            cp_async8(&hx[h], &X[j]);
-            cp_async8(&hy[h], &X[b.S + j]);
-            cp_async8(&hz[h], &X[2 * b.S + j]);
-        });
-        // the tile's lists: kmax rows of Pt entries, one contiguous block
-        const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
-        if (lstaged) {
-            const unsigned short *src = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
-            const int total = tl.kmax * Pt;            // entries; the block starts 64-byte aligned
-            const int nvec = total >> 3;
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-            uint4 *d4 = reinterpret_cast<uint4 *>(lst);
-            for (int m = threadIdx.x; m < nvec; m += blockDim.x) cp_async16(d4 + m, s4 + m);
-            for (int m = (nvec << 3) + threadIdx.x; m < total; m += blockDim.x) lst[m] = src[m];
+        if (!HALF) {   // halo and list block (the half-list pass reads no list)
+            if (own_staged)
+                for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
+            if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
+            if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
+            else stage_halo<double>(pc, np, [&](int h, int j) {
+                cp_async8(&hx[h], &X[j]);
+                cp_async8(&hy[h], &X[b.S + j]);
+                cp_async8(&hz[h], &X[2 * b.S + j]);
+            });
+            // the tile's lists: kmax rows of Pt entries, one contiguous block
+            if (tl.kmax * Pt <= kListStage * kTileMax) {
+                const unsigned short *src = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
+                const int total = tl.kmax * Pt;            // entries; the block starts 64-byte aligned
+                const int nvec = total >> 3;
+                const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+                uint4 *d4 = reinterpret_cast<uint4 *>(lst);
+                for (int m = threadIdx.x; m < nvec; m += blockDim.x) cp_async16(d4 + m, s4 + m);
+                for (int m = (nvec << 3) + threadIdx.x; m < total; m += blockDim.x) lst[m] = src[m];
+            }
+            cp_async_wait_all();
         }
-        cp_async_wait_all();
         __syncthreads();
+        const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
         double ui = 0.0, wi = 0.0, ki = 0.0;
         // FP32 path: energies as integers, twice the energy in units of 2^-22
         long long uf = 0, wf = 0, kf = 0;
@@ -547,14 +688,23 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 prefetch_l1(&X[i]); prefetch_l1(&X[b.S + i]); prefetch_l1(&X[2 * b.S + i]);
                 prefetch_l1(&b.xref[i]);
             }
-            const uint4 pi = (PREC == 1) ? hpos[s_self + (int)(i - tl.s0)] : P[i];
+            const uint4 pi = (PREC == 1 && !HALF) ? hpos[s_self + (int)(i - tl.s0)] : P[i];
             const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
             const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));   // entry k at nb[k Pt]
             double Fd[3] = {0.0, 0.0, 0.0};
             double fscale = 1.0;
             double ckick = b.half_dt_over_m;     // half kick per unit of Fd
-            if (PREC == 1) {
+            if (PREC == 1 && HALF) {
+                // the pair sums of k_pairs_half, cleared for the next step
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Fd[k] = ll_to_double(b.Fq[k * b.S + i]);
+                    b.Fq[k * b.S + i] = 0;
+                }
+                fscale = kFixInv;
+                ckick = b.half_dt_over_m_fix;
+            } else if (PREC == 1) {
                 Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 0};
                 if (lstaged) {
                     const unsigned short *nbs = lst + (i - tl.s0);
@@ -764,9 +914,14 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             block_sum3_ll(uf, kf, wf, sml);
             if (threadIdx.x == 0) {
                 long long *pl = reinterpret_cast<long long *>(b.partial);
-                pl[4 * t + 0] = uf;
+                if (HALF) {   // k_pairs_half wrote the tile's pair energy and virial
+                    pl[4 * t + 0] += uf;
+                    pl[4 * t + 2] += wf;
+                } else {
+                    pl[4 * t + 0] = uf;
+                    pl[4 * t + 2] = wf;
+                }
                 pl[4 * t + 1] = kf;
-                pl[4 * t + 2] = wf;
             }
         } else if (ENERGY) {
             double a = ui, c = ki, d = wi;
@@ -784,6 +939,106 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     constexpr bool kDrift = (MODE == kModeFused);
     if (kDrift) ratio = block_max(ratio, smr);
     finish(b, kDrift, ENERGY, true, ratio, PREC == 1);
+}
+
+// Pair pass of the half list: the tile loop of k_force (halo and list block
+// staged in shared memory), each pair once; a particle's own sum and the
+// reactions on its partners go to the fixed-point sums Fq by 64-bit atomic
+// adds.  Pair energies and virials per tile (twice the energy, as in the
+// full list, where every pair is visited from both ends).  The force kernel
+// in its half-list form then reads Fq, integrates and clears it.
+template <bool ENERGY>
+__global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Bufs b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Piece pc[kMaxPieces + 1];
+    __shared__ Tile tl;
+    __shared__ int s_tile, s_np, s_self;
+    __shared__ int s_nn[kTileMax];
+    __shared__ long long sml[kBlock / 32][3];
+    if (block_uniform(b.ctl->err != 0)) return;
+    const int cur = b.ctl->cur;
+    const double *X = b.x[cur];
+    const uint4 *P = b.pos[cur];
+    uint4 *hpos = reinterpret_cast<uint4 *>(smem_raw);
+    unsigned short *lst = reinterpret_cast<unsigned short *>(smem_raw + (size_t)b.hcap * sizeof(uint4));
+    int err = 0;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+    __syncthreads();
+    for (;;) {
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= b.ctl->ntiles) break;
+        int t_next = 0;
+        if (threadIdx.x == 0) t_next = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        load_tile(b, t, tl, pc, s_np);
+        __syncthreads();
+        const Replica &R = b.rep[tl.rep];
+        const int np = s_np;
+        const int Pt = tl.s1 - tl.s0;
+        if (pc[np].hoff > b.hcap) {
+            err |= kErrList;
+            if (threadIdx.x == 0) s_tile = t_next;
+            __syncthreads();
+            continue;
+        }
+        const bool own_staged = Pt <= kTileMax;
+        if (own_staged)
+            for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
+        if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
+        stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
+        const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
+        if (lstaged) {
+            const unsigned short *src = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
+            const int total = tl.kmax * Pt;
+            const int nvec = total >> 3;
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+            uint4 *d4 = reinterpret_cast<uint4 *>(lst);
+            for (int m = threadIdx.x; m < nvec; m += blockDim.x) cp_async16(d4 + m, s4 + m);
+            for (int m = (nvec << 3) + threadIdx.x; m < total; m += blockDim.x) lst[m] = src[m];
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // the fourth word of every staged position becomes its slot
+        stage_halo<uint4>(pc, np, [&](int h, int j) { hpos[h].w = (unsigned)j; });
+        __syncthreads();
+        long long uf = 0, kf = 0, wf = 0;
+        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+            const uint4 pi = hpos[s_self + (int)(i - tl.s0)];
+            const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
+            const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
+            // a list block too long for the stage is read from global memory
+            // through the same [row][particle] layout
+            const unsigned short *nbs = lstaged ? lst + (i - tl.s0) : b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
+            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 0};
+            if (R.cubic) neighbours32_half<ENERGY, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq);
+            else neighbours32_half<ENERGY, false>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq);
+            const unsigned hs[3] = {a.hx, a.hy, a.hz}, ls[3] = {a.lx, a.ly, a.lz};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const long long v = (long long)(int)hs[k] * 4194304LL + (long long)(int)ls[k];
+                if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.Fq + k * b.S + i), (unsigned long long)v);
+            }
+            if (ENERGY) {
+                // each pair once here: twice its energy and virial, as the
+                // full list's two visits give
+                uf += fx_round(2.0f * (R.eps4_f * a.su - R.vshift_f * (float)a.nin));
+                wf += fx_round(2.0f * (R.eps24_f * a.sg));
+            }
+        }
+        if (ENERGY) {
+            block_sum3_ll(uf, kf, wf, sml);
+            if (threadIdx.x == 0) {
+                long long *pl = reinterpret_cast<long long *>(b.partial);
+                pl[4 * t + 0] = uf;
+                pl[4 * t + 2] = wf;
+            }
+        }
+        if (threadIdx.x == 0) s_tile = t_next;
+        __syncthreads();   // the halo and the tile record are reused by the next tile
+    }
+    if (err) atomicOr(&b.ctl->err, err);
+    finish(b, false, false, true, 0.0f, true);
 }
 
 // Integrate1 of the first step of an md_step call: v += dt/2m F; x += dt v.
@@ -822,27 +1077,41 @@ static int persistent_grid(const void *fn, int block, size_t smem)
     return (occ > 0 ? occ : 1) * (nsm > 0 ? nsm : 1);
 }
 
-template <int PREC, int MODE, bool ENERGY>
+template <int PREC, int MODE, bool ENERGY, bool HALF>
 static void launch_one(const Bufs &b, cudaStream_t st)
 {
-    const size_t smem = (size_t)b.hcap * (PREC == 1 ? sizeof(uint4) : 3 * sizeof(double)) +
-                        (size_t)kListStage * kTileMax * sizeof(unsigned short);
+    const size_t smem = HALF ? 0
+                             : (size_t)b.hcap * (PREC == 1 ? sizeof(uint4) : 3 * sizeof(double)) +
+                                   (size_t)kListStage * kTileMax * sizeof(unsigned short);
     static int grid = 0;
     static size_t grid_smem = 0;
     if (grid == 0 || grid_smem != smem) {
-        grid = persistent_grid((const void *)k_force<PREC, MODE, ENERGY>, kBlock, smem);
+        grid = persistent_grid((const void *)k_force<PREC, MODE, ENERGY, HALF>, kBlock, smem);
         grid_smem = smem;
     }
-    k_force<PREC, MODE, ENERGY><<<grid, kBlock, smem, st>>>(b);
+    k_force<PREC, MODE, ENERGY, HALF><<<grid, kBlock, smem, st>>>(b);
 }
 
-template <int PREC>
+template <bool ENERGY>
+static void launch_pairs_half(const Bufs &b, cudaStream_t st)
+{
+    const size_t smem = (size_t)b.hcap * sizeof(uint4) + (size_t)kListStage * kTileMax * sizeof(unsigned short);
+    static int grid = 0;
+    static size_t grid_smem = 0;
+    if (grid == 0 || grid_smem != smem) {
+        grid = persistent_grid((const void *)k_pairs_half<ENERGY>, kBlock, smem);
+        grid_smem = smem;
+    }
+    k_pairs_half<ENERGY><<<grid, kBlock, smem, st>>>(b);
+}
+
+template <int PREC, bool HALF>
 static void launch_force_p(const Bufs &b, int mode, bool energy, cudaStream_t st)
 {
-#define MDK_CASE(M)                                        \
-    case M:                                                \
-        if (energy) launch_one<PREC, M, true>(b, st);      \
-        else launch_one<PREC, M, false>(b, st);            \
+#define MDK_CASE(M)                                              \
+    case M:                                                      \
+        if (energy) launch_one<PREC, M, true, HALF>(b, st);      \
+        else launch_one<PREC, M, false, HALF>(b, st);            \
         break;
     switch (mode) {
         MDK_CASE(kModeOut)
@@ -854,10 +1123,17 @@ static void launch_force_p(const Bufs &b, int mode, bool energy, cudaStream_t st
 #undef MDK_CASE
 }
 
+// One force evaluation in the given mode.  With a half list (FP32 only) it
+// is two kernels: the pair pass into the fixed-point sums, then the force
+// kernel's half-list form, which integrates from them.
 void launch_force(const Bufs &b, int precision, int mode, bool energy, cudaStream_t st)
 {
-    if (precision == 1) launch_force_p<1>(b, mode, energy, st);
-    else launch_force_p<0>(b, mode, energy, st);
+    if (precision == 1 && b.half_list) {
+        if (energy) launch_pairs_half<true>(b, st);
+        else launch_pairs_half<false>(b, st);
+        launch_force_p<1, true>(b, mode, energy, st);
+    } else if (precision == 1) launch_force_p<1, false>(b, mode, energy, st);
+    else launch_force_p<0, false>(b, mode, energy, st);
 }
 
 void launch_kick_drift(const Bufs &b, cudaStream_t st) { k_kick_drift<<<b.nblk, kBlock, 0, st>>>(b); }

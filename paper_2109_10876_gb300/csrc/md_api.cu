@@ -638,6 +638,9 @@ md_status md_set_state(md_handle *h, const double *x, const double *v, void *str
         !cuda_ok(h, cudaMemcpyAsync(vs, v, bytes, cudaMemcpyDefault, st), "copy velocities") ||
         !cuda_ok(h, cudaMemsetAsync(h->b.cell_count, 0, sizeof(int) * h->C, st), "clear cells"))
         return MD_ERR_CUDA;
+    // half list: a step cut short by a latched error can leave sums behind
+    if (h->b.Fq && !cuda_ok(h, cudaMemsetAsync(h->b.Fq, 0, sizeof(long long) * 3 * h->S, st), "clear force sums"))
+        return MD_ERR_CUDA;
     mdk::launch_set_state(h->b, xs, vs, st);
     if (!cuda_ok(h, cudaGetLastError(), "set_state launch")) return MD_ERR_CUDA;
     h->state_set = true;
@@ -688,6 +691,8 @@ md_status md_build_neighbors(md_handle *h, void *stream)
         }
         int zero = 0;
         if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
+            return MD_ERR_CUDA;
+        if (h->b.Fq && !cuda_ok(h, cudaMemset(h->b.Fq, 0, sizeof(long long) * 3 * h->S), "clear force sums"))
             return MD_ERR_CUDA;
         // the overflowing build still sorted the state; build again with the larger capacities
         mdk::launch_set_rebuild(h->b, st);
@@ -841,6 +846,7 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
     if (!h->state_set) return fail(h, MD_ERR_ARG, "md_forward before md_set_state");
     if (h->b.has_bonds || h->b.has_angles || h->b.langevin || h->p.potential == MD_SOFT)
         return fail(h, MD_ERR_ARG, "md_forward: the adjoint covers NVE LJ / WCA pair forces only (no bonds, angles, thermostat or push-off)");
+    if (h->b.half_list) return fail(h, MD_ERR_ARG, "md_forward: the adjoint walks the full list (md_set_half_list(h, 0))");
     cudaStream_t st = (cudaStream_t)stream;
     const long long n6 = 6LL * h->N;
     const long long nck = nsteps / ckpt_every + 1;
@@ -953,6 +959,36 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
     s = md_set_state(h, h->ad_fin, h->ad_fin + n3, st);
     if (s != MD_OK) return s;
     return sync_and_check(h, st);
+}
+
+md_status md_set_half_list(md_handle *h, int32_t enable, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    const int want = enable ? 1 : 0;
+    if (want == h->b.half_list) return MD_OK;
+    if (want && h->precision != MD_FP32_FIXED)
+        return fail(h, MD_ERR_ARG, "md_set_half_list: the half list needs MD_FP32_FIXED");
+    if (want && (h->b.has_bonds || h->b.has_angles))
+        return fail(h, MD_ERR_ARG, "md_set_half_list: the half list covers pair forces without bonds or angles");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (want && !h->b.Fq) {
+        h->b.Fq = dalloc<long long>(h, 3 * (size_t)h->S);
+        if (!h->b.Fq) return fail(h, MD_ERR_CUDA, "cannot allocate the fixed-point force sums");
+        if (!cuda_ok(h, cudaMemsetAsync(h->b.Fq, 0, sizeof(long long) * 3 * h->S, st), "clear force sums"))
+            return MD_ERR_CUDA;
+    }
+    h->b.half_list = want;
+    h->gen++;             // the step graph holds the old Bufs by value
+    h->ad_ready = false;
+    // the next call must rebuild before any force: md_step then starts from
+    // a fresh force evaluation instead of the stored one (the same values),
+    // so its first drift cannot clear the pending rebuild
+    h->F_valid = false;
+    if (h->state_set) {   // the next step, force or list call rebuilds the list in the new form
+        mdk::launch_set_rebuild(h->b, st);
+        if (!cuda_ok(h, cudaGetLastError(), "set_rebuild launch")) return MD_ERR_CUDA;
+    }
+    return MD_OK;
 }
 
 md_status md_set_tile_size(md_handle *h, int32_t tile_size, void *stream)

@@ -175,6 +175,8 @@ struct Bufs {
     double *v[2];
     uint4 *pos[2];
     double *F;               // stored total force of the current state, 3 * S, slot order
+    long long *Fq;           // half list: 64-bit fixed-point force sums (3 * S, slot order), zero between steps
+    int half_list;           // 1: each pair once (Newton's third law), reactions by 64-bit atomics
     uint4 *xref;
     int *slot_of_id;         // N
     int *cellid;             // S

@@ -116,6 +116,8 @@ _lib.md_autotune.restype = C.c_int
 _lib.md_autotune.argtypes = [_H, C.c_int32, C.POINTER(C.c_int32), _vp]
 _lib.md_set_tile_size.restype = C.c_int
 _lib.md_set_tile_size.argtypes = [_H, C.c_int32, _vp]
+_lib.md_set_half_list.restype = C.c_int
+_lib.md_set_half_list.argtypes = [_H, C.c_int32, _vp]
 _lib.md_set_timing.restype = C.c_int
 _lib.md_set_timing.argtypes = [_H, C.c_int32]
 _lib.md_get_timing.restype = C.c_int
@@ -280,6 +282,11 @@ def md_autotune(h, trial_steps=20, stream=None):
 
 def md_set_tile_size(h, tile_size, stream=None):
     return _check(h.ptr, _lib.md_set_tile_size(h.ptr, int(tile_size), _stream(stream)))
+
+
+def md_set_half_list(h, enable=True, stream=None):
+    """md_set_half_list: 1 = half list (Newton's third law), 0 = full list."""
+    return _check(h.ptr, _lib.md_set_half_list(h.ptr, 1 if enable else 0, _stream(stream)))
 
 
 def md_sync(h, stream=None):
