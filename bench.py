@@ -529,6 +529,18 @@ def main():
 
     extras = {}
     if not args.no_extras:
+        # ---- the same steps with (U, K, W) recorded every step: the energy
+        # variants of the force kernels, still one graph launch
+        thd = torch.zeros(args.steps, 3, dtype=torch.float64, device=dev)
+        md.md_step(h, 3, 1, thd)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        md.md_step(h, args.steps, 1, thd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msE = e0.elapsed_time(e1)
+        extras["energies_every_step"] = {"value": world * n * args.steps / (msE * 1e-3), "unit": UNIT,
+                                         "ms_per_step": msE / args.steps, "steps": args.steps}
         # ---- end to end through the C ABI with pinned host buffers: upload the
         # state, build, K steps with (U, K, W) every step, download the state
         xh = torch.tensor(x.T.copy()).pin_memory()

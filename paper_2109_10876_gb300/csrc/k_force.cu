@@ -189,7 +189,23 @@ __device__ void reduce_partials(const Bufs &b, double *thermo, bool fixed)
         double a = 0, c = 0, d = 0;
         if (fixed) {
             long long la = 0, lc = 0, ld = 0;
-            for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x) {
+            // four tiles per thread and round, their loads all in flight at
+            // once (integer sums: the grouping does not change the result)
+            const int q1 = b.rep_tile[r + 1], bd = blockDim.x;
+            int q = b.rep_tile[r] + threadIdx.x;
+            for (; q + 3 * bd < q1; q += 4 * bd) {
+                long long ta[4], tc[4], td[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ta[u] = pl[4 * (q + u * bd) + 0];
+                    tc[u] = pl[4 * (q + u * bd) + 1];
+                    td[u] = pl[4 * (q + u * bd) + 2];
+                }
+                la += (ta[0] + ta[1]) + (ta[2] + ta[3]);
+                lc += (tc[0] + tc[1]) + (tc[2] + tc[3]);
+                ld += (td[0] + td[1]) + (td[2] + td[3]);
+            }
+            for (; q < q1; q += bd) {
                 la += pl[4 * q + 0];
                 lc += pl[4 * q + 1];
                 ld += pl[4 * q + 2];
@@ -324,8 +340,9 @@ struct Acc32 {
     unsigned hx, lx, hy, ly, hz, lz;
     // energies: sums over the interacting pairs of s6 (s6 - 1) and
     // s6 (2 s6 - 1) (s6 = (sigma/r)^6) and their count, so that the pair
-    // energy is 4 eps su - n V(r_cut) and the virial 24 eps sg
-    float su, sg;
+    // energy is 4 eps su - n V(r_cut) and the virial 24 eps sg; two partial
+    // sums each (the lanes of the packed loop), added at the end
+    float2 su, sg;
     int nin;
 };
 
@@ -352,8 +369,8 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, b
     fx_acc2(fs, dy, a.hy, a.ly);
     fx_acc2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        a.su += in ? s6 * (s6 - 1.0f) : 0.0f;
-        a.sg += in ? g : 0.0f;
+        a.su.x += in ? s6 * (s6 - 1.0f) : 0.0f;
+        a.sg.x += in ? g : 0.0f;
         a.nin += in ? 1 : 0;
     }
 }
@@ -364,20 +381,22 @@ template <bool ENERGY>
 __device__ __forceinline__ void pair32x2(float2 dx, float2 dy, float2 dz, float2 r2, bool in0, bool in1, float sig2,
                                          float eps24, Acc32 &a)
 {
-    const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    // 1/r^2 masked to 0 outside the cutoff (and for the r = 0 padding), so
+    // that s6, g, the force scalar and the energy terms all vanish there
+    float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    ir2.x = in0 ? ir2.x : 0.0f;
+    ir2.y = in1 ? ir2.y : 0.0f;
     const float2 s2 = __fmul2_rn(make_float2(sig2, sig2), ir2);
     const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
     const float2 g = __fmul2_rn(s6, __ffma2_rn(make_float2(2.0f, 2.0f), s6, make_float2(-1.0f, -1.0f)));
-    float2 fs = __fmul2_rn(__fmul2_rn(make_float2(eps24, eps24), g), ir2);
-    fs.x = in0 ? fs.x : 0.0f;
-    fs.y = in1 ? fs.y : 0.0f;
+    const float2 fs = __fmul2_rn(__fmul2_rn(make_float2(eps24, eps24), g), ir2);
     fx_acc2x2(fs, dx, a.hx, a.lx);
     fx_acc2x2(fs, dy, a.hy, a.ly);
     fx_acc2x2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
         const float2 e = __fmul2_rn(s6, __fadd2_rn(s6, make_float2(-1.0f, -1.0f)));
-        a.su += (in0 ? e.x : 0.0f) + (in1 ? e.y : 0.0f);
-        a.sg += (in0 ? g.x : 0.0f) + (in1 ? g.y : 0.0f);
+        a.su = __fadd2_rn(a.su, e);
+        a.sg = __fadd2_rn(a.sg, g);
         a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
     }
 }
@@ -502,13 +521,15 @@ __device__ __forceinline__ void pair32x2_half(float2 dx, float2 dy, float2 dz, f
                                               float sig2, float eps24, Acc32 &a, long long *Fq, long long S,
                                               unsigned s0, unsigned s1)
 {
-    const float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    // 1/r^2 masked to 0 outside the cutoff (and for the r = 0 padding), so
+    // that s6, g, the force scalar and the energy terms all vanish there
+    float2 ir2 = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+    ir2.x = in0 ? ir2.x : 0.0f;
+    ir2.y = in1 ? ir2.y : 0.0f;
     const float2 s2 = __fmul2_rn(make_float2(sig2, sig2), ir2);
     const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
     const float2 g = __fmul2_rn(s6, __ffma2_rn(make_float2(2.0f, 2.0f), s6, make_float2(-1.0f, -1.0f)));
-    float2 fs = __fmul2_rn(__fmul2_rn(make_float2(eps24, eps24), g), ir2);
-    fs.x = in0 ? fs.x : 0.0f;
-    fs.y = in1 ? fs.y : 0.0f;
+    const float2 fs = __fmul2_rn(__fmul2_rn(make_float2(eps24, eps24), g), ir2);
     long long x0, x1, y0, y1, z0, z1;
     fx_acc2x2_v(fs, dx, a.hx, a.lx, x0, x1);
     fx_acc2x2_v(fs, dy, a.hy, a.ly, y0, y1);
@@ -517,8 +538,8 @@ __device__ __forceinline__ void pair32x2_half(float2 dx, float2 dy, float2 dz, f
     if (in1) { red_sub(Fq + s1, x1); red_sub(Fq + S + s1, y1); red_sub(Fq + 2 * S + s1, z1); }
     if (ENERGY) {
         const float2 e = __fmul2_rn(s6, __fadd2_rn(s6, make_float2(-1.0f, -1.0f)));
-        a.su += (in0 ? e.x : 0.0f) + (in1 ? e.y : 0.0f);
-        a.sg += (in0 ? g.x : 0.0f) + (in1 ? g.y : 0.0f);
+        a.su = __fadd2_rn(a.su, e);
+        a.sg = __fadd2_rn(a.sg, g);
         a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
     }
 }
@@ -705,7 +726,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 fscale = kFixInv;
                 ckick = b.half_dt_over_m_fix;
             } else if (PREC == 1) {
-                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 0};
+                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
                 if (lstaged) {
                     const unsigned short *nbs = lst + (i - tl.s0);
                     if (R.cubic) neighbours32<ENERGY, true, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
@@ -722,8 +743,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 ckick = b.half_dt_over_m_fix;
                 if (ENERGY) {
                     // twice this particle's pair energy and virial, in FP32, to fixed point
-                    uf += fx_round(R.eps4_f * a.su - R.vshift_f * (float)a.nin);
-                    wf += fx_round(R.eps24_f * a.sg);
+                    uf += fx_round(R.eps4_f * (a.su.x + a.su.y) - R.vshift_f * (float)a.nin);
+                    wf += fx_round(R.eps24_f * (a.sg.x + a.sg.y));
                 }
             } else {
                 const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
@@ -1010,7 +1031,7 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
             // a list block too long for the stage is read from global memory
             // through the same [row][particle] layout
             const unsigned short *nbs = lstaged ? lst + (i - tl.s0) : b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
-            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 0};
+            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
             if (R.cubic) neighbours32_half<ENERGY, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq);
             else neighbours32_half<ENERGY, false>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq);
             const unsigned hs[3] = {a.hx, a.hy, a.hz}, ls[3] = {a.lx, a.ly, a.lz};
@@ -1022,8 +1043,8 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
             if (ENERGY) {
                 // each pair once here: twice its energy and virial, as the
                 // full list's two visits give
-                uf += fx_round(2.0f * (R.eps4_f * a.su - R.vshift_f * (float)a.nin));
-                wf += fx_round(2.0f * (R.eps24_f * a.sg));
+                uf += fx_round(2.0f * (R.eps4_f * (a.su.x + a.su.y) - R.vshift_f * (float)a.nin));
+                wf += fx_round(2.0f * (R.eps24_f * (a.sg.x + a.sg.y)));
             }
         }
         if (ENERGY) {
