@@ -12,6 +12,7 @@ What each function follows in arXiv:2109.10876:
   forces                    direct O(N^2) minimum-image pair sum under r < r_cut
   forces_sample             the same sum for chosen particles only
   pairs                     the Verlet pair set within r_cut + r_skin (Sec. 2.1.2)
+  neighbours_sample         the same set's rows for chosen particles only
   vv_run                    velocity Verlet in two half steps (Fig. 1)
   philox4x32_10             counter-based generator (Salmon et al., SC'11) for the
                             Langevin noise (Sec. 4 names the thermostat only)
@@ -78,6 +79,9 @@ def lib():
         L.orc_pairs.restype = C.c_int64
         L.orc_pairs.argtypes = [sp, dp, C.c_double, C.c_int64,
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.orc_neighbours_sample.restype = C.c_int64
+        L.orc_neighbours_sample.argtypes = [sp, dp, C.c_double, C.c_int64, C.POINTER(C.c_int64), C.c_int64,
+                                            C.POINTER(C.c_int32), dp, C.POINTER(C.c_int32)]
         L.orc_philox4x32_10.restype = None
         L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                         C.POINTER(C.c_uint32)]
@@ -242,6 +246,30 @@ def pairs(sysm, x, r):
                          out.ctypes.data_as(C.POINTER(C.c_int32)), None)
     assert m2 == m
     return out[:m], counts
+
+
+def neighbours_sample(sysm, x, idx, r):
+    """Neighbours within r of the particles idx, by brute force over all j
+    (the rows of the pair set of Sec. 2.1.2 for those particles).
+
+    Returns a list with, per sampled particle, (j (ascending int array),
+    r^2 of each pair (FP64, the formula of `pairs`))."""
+    x = _f64(x, (sysm.n, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    counts = np.zeros(len(idx), dtype=np.int32)
+    s = sysm.c()
+    ip = idx.ctypes.data_as(C.POINTER(C.c_int64))
+    mx = lib().orc_neighbours_sample(C.byref(s), _dp(x), float(r), len(idx), ip, 0, None, None,
+                                     counts.ctypes.data_as(C.POINTER(C.c_int32)))
+    if mx < 0:
+        raise ValueError("neighbours_sample: index out of range")
+    cap = max(int(mx), 1)
+    nbr = np.zeros((len(idx), cap), dtype=np.int32)
+    r2 = np.zeros((len(idx), cap))
+    lib().orc_neighbours_sample(C.byref(s), _dp(x), float(r), len(idx), ip, cap,
+                                nbr.ctypes.data_as(C.POINTER(C.c_int32)), _dp(r2),
+                                counts.ctypes.data_as(C.POINTER(C.c_int32)))
+    return [(nbr[q, :counts[q]].copy(), r2[q, :counts[q]].copy()) for q in range(len(idx))]
 
 
 def philox4x32_10(ctr, key):

@@ -435,6 +435,43 @@ int64_t orc_pairs(const orc_system *s, const double *x, double r, int64_t cap,
     return m;
 }
 
+/* Neighbours of chosen particles (the rows of the Verlet pair set of       */
+/* Sec. 2.1.2 for those particles): for sample q, every j != idx[q] with   */
+/* |d_ij| < r, in increasing j, and its r^2 (the same FP64 formula as       */
+/* orc_pairs).  Brute force over all j, one sample per thread.  counts[q]   */
+/* gets the number of neighbours; at most cap of them are written to        */
+/* nbr[q * cap ...] and r2[q * cap ...] (either may be NULL).  Returns the  */
+/* largest count.                                                           */
+int64_t orc_neighbours_sample(const orc_system *s, const double *x, double r, int64_t n_sample,
+                              const int64_t *idx, int64_t cap, int32_t *nbr, double *r2out,
+                              int32_t *counts)
+{
+    const double r2c = r * r;
+    for (int64_t q = 0; q < n_sample; ++q)
+        if (idx[q] < 0 || idx[q] >= s->n) return -1;
+    int64_t mx = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(max : mx)
+    for (int64_t q = 0; q < n_sample; ++q) {
+        const int64_t i = idx[q];
+        int64_t m = 0;
+        for (int64_t j = 0; j < s->n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            const double r2 = min_image(&x[3 * i], &x[3 * j], s->box, d);
+            if (r2 < r2c) {
+                if (m < cap) {
+                    if (nbr) nbr[q * cap + m] = (int32_t)j;
+                    if (r2out) r2out[q * cap + m] = r2;
+                }
+                ++m;
+            }
+        }
+        counts[q] = (int32_t)m;
+        if (m > mx) mx = m;
+    }
+    return mx;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -155,6 +155,31 @@ def test_fcc_4000_pins():
     assert euw[0] / 4000 == pytest.approx(shell, rel=1e-12)
 
 
+def test_neighbours_sample_pins():
+    """Sampled neighbour rows: on the fcc lattice every site has the 78
+    neighbours of the first five shells, at the shell distances a sqrt(m/2);
+    on a random gas in a small box (pairs across the boundary) the rows are
+    exactly those of the brute-force pair set."""
+    x, box = inputs.fcc_lattice(10, 0.8442)
+    s = oracle.System(len(x), box, rc=RC)
+    a = (4 / 0.8442) ** (1 / 3)
+    for j, r2 in oracle.neighbours_sample(s, x, [0, 1, 1234, 3999], RC + SKIN):
+        assert len(j) == 78 and np.all(np.diff(j) > 0)
+        m = np.round(2 * r2 / a ** 2).astype(int)
+        np.testing.assert_allclose(r2, a ** 2 * m / 2, rtol=1e-12)
+        assert [int(np.sum(m == k)) for k in range(1, 6)] == [c for k, _, c in _fcc_golden() if k <= 5]
+    box = np.array([6.3, 6.6, 6.1])
+    x = inputs.random_gas(300, box, seed=77)
+    s = oracle.System(300, box, rc=RC)
+    pr, _ = oracle.pairs(s, x, RC + SKIN)
+    rows = oracle.neighbours_sample(s, x, np.arange(300), RC + SKIN)
+    for i in range(300):
+        want = np.sort(np.concatenate([pr[pr[:, 0] == i, 1], pr[pr[:, 1] == i, 0]]))
+        np.testing.assert_array_equal(rows[i][0], want)
+        for j, r2 in zip(*rows[i]):
+            assert r2 == oracle.min_image_r2(x[i], x[j], box)
+
+
 def test_cell_rule_from_paper():
     """N = 262144 at rho = 0.8442 gives a 24^3 cell grid with cell edge >= r_cut + r_skin
     (Sec. 5 quotes the (24, 24, 24) grid)."""
