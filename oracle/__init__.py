@@ -11,6 +11,7 @@ What each function follows in arXiv:2109.10876:
   angle_triple              cosine angle term on chain triples (Sec. 4)
   forces                    direct O(N^2) minimum-image pair sum under r < r_cut
   forces_sample             the same sum for chosen particles only
+  bonded_sample             FENE and angle forces (Sec. 4) on chosen particles
   pairs                     the Verlet pair set within r_cut + r_skin (Sec. 2.1.2)
   neighbours_sample         the same set's rows for chosen particles only
   vv_run                    velocity Verlet in two half steps (Fig. 1)
@@ -74,6 +75,10 @@ def lib():
         L.orc_forces.argtypes = [sp, dp, dp, dp, dp]
         L.orc_forces_sample.restype = C.c_int
         L.orc_forces_sample.argtypes = [sp, dp, C.c_int64, C.POINTER(C.c_int64), dp, dp, dp]
+        L.orc_bonded_sample.restype = C.c_int
+        L.orc_bonded_sample.argtypes = [sp, dp, C.c_int64, C.POINTER(C.c_int64), dp]
+        L.orc_langevin_sample.restype = None
+        L.orc_langevin_sample.argtypes = [sp, C.c_int64, C.POINTER(C.c_int64), dp, C.c_int64, dp]
         L.orc_vv_run.restype = C.c_int
         L.orc_vv_run.argtypes = [sp, dp, dp, dp, C.c_int64, C.c_int64, dp]
         L.orc_pairs.restype = C.c_int64
@@ -218,6 +223,19 @@ def forces_sample(sysm, x, idx):
     return F, ui, wi
 
 
+def bonded_sample(sysm, x, idx):
+    """FENE and angle-term forces (Sec. 4) on particles idx only, (n, 3).
+    Raises on a broken bond."""
+    x = _f64(x, (sysm.n, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    F = np.zeros((len(idx), 3))
+    s = sysm.c()
+    rc = lib().orc_bonded_sample(C.byref(s), _dp(x), len(idx), idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(F))
+    if rc != 0:
+        raise RuntimeError(f"oracle bonded_sample failed: {rc}")
+    return F
+
+
 def vv_run(sysm, x, v, nsteps, step0=0, thermo=False):
     """Velocity Verlet from (x, v); returns (x, v, F[, thermo (nsteps,3)])."""
     x = _f64(x, (sysm.n, 3)).copy()
@@ -284,6 +302,19 @@ def langevin_uniforms(seed, pid, step):
     u = np.zeros(3)
     lib().orc_langevin_uniforms(int(seed), int(pid), int(step), _dp(u))
     return u
+
+
+def langevin_sample(sysm, idx, v_idx, step):
+    """The Langevin force -gamma m v + sqrt(24 gamma kT m / dt) u (u from
+    Philox, keyed by the seed, the particle and the step) on particles idx
+    with velocities v_idx (n, 3)."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    vv = _f64(v_idx, (len(idx), 3))
+    F = np.zeros((len(idx), 3))
+    s = sysm.c()
+    lib().orc_langevin_sample(C.byref(s), len(idx), idx.ctypes.data_as(C.POINTER(C.c_int64)), _dp(vv),
+                              int(step), _dp(F))
+    return F
 
 
 def hvp(sysm, x, w):

@@ -335,6 +335,46 @@ int orc_forces_sample(const orc_system *s, const double *x, int64_t n_sample,
     return ORC_OK;
 }
 
+/* Bonded forces (FENE bonds and angle triples, Sec. 4) on chosen particles: */
+/* for each sample, the bonds and triples it belongs to are found by a scan  */
+/* of the whole bond and triple lists, and their forces on it summed.  The   */
+/* counterpart of orc_forces_sample for the bonded terms; Fs is n_sample x 3. */
+int orc_bonded_sample(const orc_system *s, const double *x, int64_t n_sample,
+                      const int64_t *idx, double *Fs)
+{
+    for (int64_t q = 0; q < n_sample; ++q)
+        if (idx[q] < 0 || idx[q] >= s->n) return ORC_ERR_ARG;
+    int rc = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_sample; ++q) {
+        const int64_t i = idx[q];
+        double F[3] = {0, 0, 0};
+        for (int64_t b = 0; b < s->n_bonds && s->bonds; ++b) {
+            const int64_t a = s->bonds[2 * b], c = s->bonds[2 * b + 1];
+            if (a != i && c != i) continue;
+            const int64_t j = (a == i) ? c : a;
+            double d[3], f[3], u, w;
+            const double r2 = min_image(&x[3 * i], &x[3 * j], s->box, d);
+            if (fene_pair(s, d, r2, f, &u, &w) != ORC_OK) {
+#pragma omp atomic write
+                rc = ORC_ERR_BOND;
+                continue;
+            }
+            for (int k = 0; k < 3; ++k) F[k] += f[k];
+        }
+        for (int64_t t = 0; t < s->n_angles && s->angles; ++t) {
+            const int64_t a = s->angles[3 * t], b = s->angles[3 * t + 1], c = s->angles[3 * t + 2];
+            if (a != i && b != i && c != i) continue;
+            double fa[3], fb[3], fc[3], u;
+            orc_angle_triple(&x[3 * a], &x[3 * b], &x[3 * c], s->box, s->angle_K, fa, fb, fc, &u);
+            const double *f = (a == i) ? fa : (b == i ? fb : fc);
+            for (int k = 0; k < 3; ++k) F[k] += f[k];
+        }
+        for (int k = 0; k < 3; ++k) Fs[3 * q + k] = F[k];
+    }
+    return rc;
+}
+
 /* Langevin force on particle i at a given step, using velocity vi. */
 static void langevin_force(const orc_system *s, int64_t i, int64_t step, const double *vi, double f[3])
 {
@@ -342,6 +382,14 @@ static void langevin_force(const orc_system *s, int64_t i, int64_t step, const d
     orc_langevin_uniforms(s->seed, i, step, u);
     double amp = sqrt(24.0 * s->gamma * s->kT * s->mass / s->dt);
     for (int k = 0; k < 3; ++k) f[k] = -s->gamma * s->mass * vi[k] + amp * u[k];
+}
+
+/* The Langevin force of chosen particles at a given step, with their       */
+/* velocities vs (n_sample x 3) as the integrator would use them.            */
+void orc_langevin_sample(const orc_system *s, int64_t n_sample, const int64_t *idx, const double *vs,
+                         int64_t step, double *Fs)
+{
+    for (int64_t q = 0; q < n_sample; ++q) langevin_force(s, idx[q], step, &vs[3 * q], &Fs[3 * q]);
 }
 
 /* Total force used by the integrator: conservative + (if gamma > 0) Langevin. */

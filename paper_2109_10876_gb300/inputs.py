@@ -158,19 +158,24 @@ def rsa_fast(n, box, lo, hi, rmin, rng, existing=None, batch=20000):
         grid[k] = np.arange(len(existing))
         m = len(existing)
     start = m
-    offs = np.array([(a, b, c) for a in range(-2, 3) for b in range(-2, 3) for c in range(-2, 3)])
+    o5 = np.arange(-2, 3)
     tries = 0
     while m - start < n:
         cand = lo + rng.uniform(0.0, 1.0, size=(batch, 3)) * (hi - lo)
         cand = np.mod(cand, box)
         _, cc = cell_of(cand)
-        nb = (cc[:, None, :] + offs[None, :, :]) % ng
-        nbk = (nb[..., 2] * ng[1] + nb[..., 1]) * ng[0] + nb[..., 0]
+        # the 5 x 5 x 5 cells around each candidate, wrapped per axis
+        ax = [(cc[:, k, None] + o5[None, :]) % ng[k] for k in range(3)]
+        nbk = ((ax[2][:, None, None, :] * ng[1] + ax[1][:, None, :, None]) * ng[0] +
+               ax[0][:, :, None, None]).reshape(len(cand), 125)
         idx = grid[nbk]                                   # (batch, 125)
-        d = cand[:, None, :] - pts[np.maximum(idx, 0)]
+        # distances to the occupied cells only (most of the 125 are empty)
+        row, col = np.nonzero(idx >= 0)
+        d = cand[row] - pts[idx[row, col]]
         d -= box * np.round(d / box)
-        close = (np.sum(d * d, axis=2) < rmin * rmin) & (idx >= 0)
-        ok = ~close.any(axis=1)
+        close = np.zeros(len(cand), dtype=bool)
+        close[row[np.sum(d * d, axis=1) < rmin * rmin]] = True
+        ok = ~close
         good = np.nonzero(ok)[0]
         # conflicts among this batch's survivors: keep the earlier candidate
         if len(good) > 1:

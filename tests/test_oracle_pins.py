@@ -180,6 +180,41 @@ def test_neighbours_sample_pins():
             assert r2 == oracle.min_image_r2(x[i], x[j], box)
 
 
+def test_bonded_sample_pins():
+    """Bonded forces of chosen particles: one FENE bond along x gives
+    F = -K r / (1 - r^2/R0^2) on its first particle and the opposite on the
+    second; on chains with angle triples, the sampled non-bonded plus bonded
+    forces equal the whole-system oracle forces."""
+    box = np.array([8.0, 8.0, 8.0])
+    r = 1.1
+    x = np.array([[1.0, 2.0, 3.0], [1.0 + r, 2.0, 3.0]])
+    s = oracle.System(2, box, rc=2 ** (1 / 6), bonds=np.array([[0, 1]]), fene_K=30.0, fene_R0=1.5)
+    Fb = oracle.bonded_sample(s, x, [0, 1])
+    f = 30.0 * r / (1 - r * r / 2.25)
+    np.testing.assert_allclose(Fb, [[f, 0, 0], [-f, 0, 0]], rtol=1e-14)
+    box = np.array([9.0, 9.0, 9.0])
+    x, bonds = inputs.chains(6, 20, box, seed=5)
+    ang = np.array([[c * 20 + k - 1, c * 20 + k, c * 20 + k + 1] for c in range(6) for k in range(1, 19)])
+    s = oracle.System(len(x), box, rc=2 ** (1 / 6), bonds=bonds, angles=ang, angle_K=1.5)
+    F, _ = oracle.forces(s, x)
+    idx = np.arange(len(x))
+    Fn, _, _ = oracle.forces_sample(s, x, idx)
+    np.testing.assert_allclose(Fn + oracle.bonded_sample(s, x, idx), F, rtol=0, atol=1e-12 * np.max(np.abs(F)))
+
+
+def test_langevin_sample_fluctuation_dissipation():
+    """The sampled Langevin force has mean -gamma m v (the friction) and
+    variance 2 gamma kT m / dt per component (the fluctuation-dissipation
+    relation of the force-form thermostat), over 200000 particle draws."""
+    n = 200_000
+    s = oracle.System(n, [50.0, 50.0, 50.0], gamma=0.5, kT=1.3, mass=1.0, dt=0.01, seed=11)
+    v = np.random.default_rng(3).normal(size=(n, 3))
+    F = oracle.langevin_sample(s, np.arange(n), v, 17)
+    noise = F + 0.5 * 1.0 * v
+    assert abs(noise.mean()) < 5 * math.sqrt(2 * 0.5 * 1.3 / 0.01 / (3 * n))
+    assert noise.var() == pytest.approx(2 * 0.5 * 1.3 / 0.01, rel=0.01)
+
+
 def test_cell_rule_from_paper():
     """N = 262144 at rho = 0.8442 gives a 24^3 cell grid with cell edge >= r_cut + r_skin
     (Sec. 5 quotes the (24, 24, 24) grid)."""
