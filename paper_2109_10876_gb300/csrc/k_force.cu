@@ -59,6 +59,16 @@ __device__ __forceinline__ void fx_acc2x2(float2 a, float2 c, unsigned &hi, unsi
     lo += __float_as_uint(t2.x) + __float_as_uint(t2.y);
 }
 
+// One 16-byte shared-memory load of a staged halo position (the compiler
+// would otherwise split it when the fourth word is not used).
+__device__ __forceinline__ uint4 lds128(const uint4 *p)
+{
+    uint4 q;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w) : "r"(a));
+    return q;
+}
+
 // Reciprocal by the hardware approximation (a pure function of its input).
 __device__ __forceinline__ float rcp_approx(float x)
 {
@@ -431,7 +441,7 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
         for (int u = 0; u < kU; ++u) hh[u] = LSMEM ? nb[(k0 + u) * Pt] : __ldg(nb + (long long)(k0 + u) * Pt);
 #pragma unroll
         for (int u = 0; u < kU; u += 2) {
-            const uint4 q0 = hpos[hh[u]], q1 = hpos[hh[u + 1]];
+            const uint4 q0 = lds128(hpos + hh[u]), q1 = lds128(hpos + hh[u + 1]);
             float2 dx = make_float2((float)(int)(pi.x - q0.x), (float)(int)(pi.x - q1.x));
             float2 dy = make_float2((float)(int)(pi.y - q0.y), (float)(int)(pi.y - q1.y));
             float2 dz = make_float2((float)(int)(pi.z - q0.z), (float)(int)(pi.z - q1.z));
