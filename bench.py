@@ -39,6 +39,12 @@ RHO, T0, RC, SKIN, DT = 0.8442, 0.72, 2.5, 0.3, 0.005
 # besides the list: own fixed-point position 16, list length 4, x read+write 48,
 # v read+write 48, new fixed-point position 16, build-time position 16
 FORCE_FIXED_BYTES = 16 + 4 + 48 + 48 + 16 + 16
+# FP64 path, algorithmic FP64 operations per list entry: separation 3,
+# minimum image 3, r^2 5, cutoff test 1 (12 for an entry beyond r_cut); an
+# interacting pair adds 1/r^2 1, (sigma/r)^2 1, ^6 2, force scalar 4, force
+# accumulation 6 (26 in all)
+FP64_OPS_OUT, FP64_OPS_IN = 12, 26
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 nominal FP64 rate (no measured FP64 peak on this machine)
 # the half list adds, per particle, the fixed-point force sums: 24 B written
 # by the pair pass (the atomics' net result), 24 B read and 24 B cleared by
 # the integrating pass
@@ -198,6 +204,48 @@ def cpu_baseline(x, box, target_s=10.0):
     return {"value": S / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"exact FP64 O(N^2) forces on {S} sampled particles of the N={n} system "
                       f"(one particle-step each), {t:.1f} s"}
+
+
+def config_4000_leg(md, torch, dev, e0, e1, stream):
+    """The small LJ fluid (N = 4000, fcc 10^3 x 4, T* 0.72, seed 1), 100 FP64
+    velocity-Verlet steps at dt 0.005: the GPU's plain FP64 path (CUDA events)
+    beside the FP64 oracle's own full run of the same steps (exact O(N^2)
+    forces every step) on all host cores and on one, and the largest position
+    difference between the two."""
+    import oracle
+    from paper_2109_10876_gb300 import inputs
+    x, v, box = inputs.lj_fluid(10, rho=RHO, T=T0, seed=1)
+    n = len(x)
+    h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP64)
+    md.md_set_state(h, torch.tensor(x.T.copy(), device=dev), torch.tensor(v.T.copy(), device=dev))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    md.md_build_neighbors(h)
+    md.md_step(h, 100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_gpu = e0.elapsed_time(e1)
+    xo = torch.zeros(3, n, dtype=torch.float64, device=dev)
+    md.md_get_state(h, xo, None)
+    xg = xo.cpu().numpy().T
+    h.destroy()
+    s = oracle.System(n, box, rc=RC, dt=DT)
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    xr, _, _ = oracle.vv_run(s, x, v, 100)
+    t_all = time.perf_counter() - t0
+    oracle.set_num_threads(1)
+    t0 = time.perf_counter()
+    oracle.vv_run(s, x, v, 100)
+    t_one = time.perf_counter() - t0
+    oracle.set_num_threads(cores)
+    d = xg - xr
+    d -= box * np.round(d / box)
+    return {"steps": 100, "particles": n, "gpu_fp64_ms": ms_gpu, "gpu_fp64_value": n * 100 / (ms_gpu * 1e-3),
+            "oracle_s": t_all, "oracle_cores": cores, "oracle_value": n * 100 / t_all,
+            "oracle_1core_s": t_one, "oracle_1core_value": n * 100 / t_one,
+            "max_abs_dx_gpu_vs_oracle": float(np.max(np.abs(d))), "unit": UNIT,
+            "note": "GPU time includes the first list build; the oracle sums all pairs every step"}
 
 
 def ensemble_leg(md, torch, dev, passes=3, nsteps=200, ckpt=20):
@@ -589,8 +637,18 @@ def main():
         ms64 = e0.elapsed_time(e1)
         h3.destroy()
         v64 = n * k64 / (ms64 * 1e-3)
+        # algorithmic FP64 rate of the pair sums: list entries from the timed
+        # run's mean length, interacting pairs from the density (4/3 pi rc^3 rho)
+        n_in = 4.0 / 3.0 * math.pi * RC ** 3 * RHO
+        ops = n * (n_in * FP64_OPS_IN + max(mean_nn - n_in, 0.0) * FP64_OPS_OUT)
+        tf = ops / (ms64 / k64 * 1e-3) / 1e12
         extras["fp64"] = {"value": world * v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
-                          "speedup_fp32_fixed_over_fp64": (value / world) / v64}
+                          "speedup_fp32_fixed_over_fp64": (value / world) / v64,
+                          "pair_tflops": round(tf, 4), "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
+                          "frac_of_nominal_fp64": round(tf / FP64_NOMINAL_TFLOPS, 4),
+                          "ops_per_step": ops,
+                          "note": "FP64 operations of the pair sums by count per list entry (12 beyond r_cut, 26 "
+                                  "within), against the nominal FP64 rate; the FP64 path also integrates in FP64"}
 
         # ---- the other list form on the same input (Sec. 2.1.2: the half list
         # of Newton's third law against the full list)
@@ -643,6 +701,7 @@ def main():
                                                                            np.maximum(mag, rms))),
                                      "input": "fcc lattice with uniform +-0.1 sigma displacements"}
             extras["cpu_baseline"] = cpu_baseline(x, box)
+            extras["lj_fluid_4000"] = config_4000_leg(md, torch, dev, e0, e1, stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -101,6 +101,8 @@ def lib():
         L.orc_set_rc_fixed.restype = None
         L.orc_set_rc_fixed.argtypes = [C.c_int]
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.restype = None
+        L.orc_set_num_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -349,3 +351,8 @@ def vv_adjoint(sysm, x, v, nsteps, cU, cK, cW, rc_fixed=False):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().orc_set_num_threads(int(n))

@@ -520,6 +520,16 @@ int64_t orc_neighbours_sample(const orc_system *s, const double *x, double r, in
     return mx;
 }
 
+/* Thread count of the OpenMP loops that follow (0 or less: leave as is). */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
