@@ -87,9 +87,10 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(digest):
-    """DRAM bytes per particle of the fused force kernel from the committed ncu
-    summary, if it was taken on the current kernel sources; else None."""
+def profiled(digest, key):
+    """A per-particle figure of the fused force kernel (DRAM bytes, warp
+    instructions) from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
     p = os.path.join(ROOT, "profiles", "force_fp32_fused_lj_fluid.md")
     if not os.path.exists(p):
         return None
@@ -101,9 +102,13 @@ def profiled_traffic(digest):
     if vals.get("csrc_sha") != digest:
         return None
     try:
-        return float(vals["dram_bytes_per_particle"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic(digest):
+    return profiled(digest, "dram_bytes_per_particle")
 
 
 class Clocks:
@@ -567,6 +572,20 @@ def main():
     peak, peak_kind = measured_peaks()
     digest = csrc_digest()
     tpp = profiled_traffic(digest)
+    # the resource that binds the kernel in practice: instruction issue (four
+    # schedulers per SM, one warp instruction each per cycle), from the profiled
+    # warp instructions per particle and the live launch time
+    ipp = profiled(digest, "warp_instructions_per_particle")
+    issue = None
+    if ipp is not None and not half:
+        sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = n * ipp / (force_ms * 1e-3)
+        pk = 4.0 * nsm * sm_mhz * 1e6
+        issue = {"bound": "issue", "achieved": round(ach / 1e9, 1), "peak": round(pk / 1e9, 1),
+                 "unit": "G warp-instructions/s", "frac": round(ach / pk, 4),
+                 "note": "4 schedulers x the SMs x the median SM clock under load; warp instructions "
+                         "per particle from the committed ncu summary of this kernel's sources"}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": None if (tpp is None or half) else round(tpp * n),
@@ -716,6 +735,7 @@ def main():
                            "l2": "working set larger than L2 (positions, velocities and the Verlet list: "
                                  f"~{(n * (FORCE_FIXED_BYTES + list_bytes)) / 1e6:.0f} MB touched per step)"},
                 "roofline": roofline,
+                "issue_roofline": issue,
                 "gpu_launches": (3 if half else 2) * args.steps + 3 +
                                 REBUILD_KERNELS * (st1["rebuilds"] - st0["rebuilds"]),
                 "rebuilds": st1["rebuilds"] - st0["rebuilds"],
