@@ -17,7 +17,7 @@
  *   - velocity Verlet in two half steps (Integrate1 / Integrate2)   (Fig. 1, Sec. 2.1)
  *   - FENE bonds along chains, Langevin thermostat                  (Sec. 4)
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - the LJ energy is shifted so that V_s(r_cut) = 0 (forces unchanged);
  *     WCA is the same shifted form with r_cut = 2^(1/6) sigma, i.e. V + eps;
  *   - the Langevin thermostat is a force term -gamma m v + sqrt(24 gamma kT m/dt) u,
