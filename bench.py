@@ -321,6 +321,11 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra):
     md.md_sync(h)
     ms, st0, st1, ck = timed_steps(md, torch, h, args.steps, stream)
     rb = st1["rebuilds"] - st0["rebuilds"]
+    # a second pass of the same length with per-launch events: where the time goes
+    md.md_set_timing(h, True)
+    md.md_step(h, args.steps)
+    sect_ms, _ = md.md_get_timing(h)
+    md.md_set_timing(h, False)
     line = {"metric": f"{name} particle-steps/s", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -329,7 +334,11 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra):
             "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + REBUILD_KERNELS * rb,
             "mean_list_len": st1["list_entries"] / n, "max_list_len": st1["max_list_len"],
             "max_cell_occupancy": st1["max_cell_occupancy"], "tiles": st1["n_tiles"],
-            "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck}
+            "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck,
+            "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / args.steps,
+                                     "force_integrate": sect_ms[md.MD_SECT_FORCE] / args.steps,
+                                     "other": sect_ms[md.MD_SECT_OTHER] / args.steps,
+                                     "note": "second pass with per-launch events"}}
     print(json.dumps(line), flush=True)
 
 

@@ -75,6 +75,25 @@ def test_pair_set_random(md, n, boxl, seed):
     np.testing.assert_array_equal(got.reshape(-1, 2), want.reshape(-1, 2))
 
 
+@pytest.mark.parametrize("half", [False, True])
+def test_pair_set_short_lists(md, half):
+    """A melt of free random-walk chains (2000 beads at density 0.85, overlaps
+    left in) with the WCA list radius 2^(1/6) + 0.4: short lists (about 12
+    entries) from cells of three particles; the list (full or half) equals the
+    brute-force pair set."""
+    x, v, box, bonds = inputs.melt(40, 50, rho=0.85, T=1.0, seed=19)
+    n = len(x)
+    rl = 2 ** (1 / 6) + 0.4
+    h = md.md_create(n, box, potential=md.MD_WCA, skin=0.4, precision=md.MD_FP32_FIXED)
+    if half:
+        md.md_set_half_list(h, True)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    got = md.export_pairs_sorted(h)
+    want, _ = oracle.pairs(oracle.System(n, box, rc=2 ** (1 / 6)), x, rl)
+    np.testing.assert_array_equal(got, want)
+
+
 # ----------------------------------------------------------------- forces
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", ["liquid", "fcc", "gas_small_box"])
