@@ -315,7 +315,10 @@ def timed_steps(md, torch, h, steps, stream):
     return e0.elapsed_time(e1), st0, st1, ck
 
 
-def workload_line(md, torch, dev, args, name, n, h, prep, extra):
+def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=None):
+    # systems with bonds or angle triples add one kernel to each rebuild (the
+    # slots of their partners)
+    chain_kernels = REBUILD_KERNELS if chain_kernels is None else chain_kernels
     stream = torch.cuda.current_stream()
     md.md_step(h, max(args.warmup, 3))
     md.md_sync(h)
@@ -331,7 +334,7 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+fixed64 (f64 integration)", "data": "synthetic",
             "config": dict(extra, particles=n, tile_size=st1["tile_size"]),
-            "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + REBUILD_KERNELS * rb,
+            "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + chain_kernels * rb,
             "mean_list_len": st1["list_entries"] / n, "max_list_len": st1["max_list_len"],
             "max_cell_occupancy": st1["max_cell_occupancy"], "tiles": st1["n_tiles"],
             "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck,
@@ -379,7 +382,8 @@ def run_melt(md, torch, dev, args):
     workload_line(md, torch, dev, args, "polymer melt", n, h, prep,
                   {"workload": f"Kremer-Grest melt, 2000 x 200 linear chains (N = {n}), bead density 0.85, "
                                f"WCA + FENE (K 30, R0 1.5) + Langevin (gamma 0.5, T 1), dt 0.01, skin 0.4",
-                   "l2": "working set about 60 MB (below L2); the timed steps run back to back"})
+                   "l2": "working set about 60 MB (below L2); the timed steps run back to back"},
+                  chain_kernels=REBUILD_KERNELS + 1)
     h.destroy()
 
 
@@ -423,7 +427,8 @@ def run_rings(md, torch, dev, args):
                   {"workload": f"ring polymer melt, 1600 x 200 (N = {n}), bead density 0.85, WCA + FENE "
                                f"(K 30, R0 1.5) + cosine angle (K 1.5) + Langevin (gamma 0.5, T 1), dt 0.005, "
                                f"skin 0.4",
-                   "l2": "working set about 50 MB (below L2); the timed steps run back to back"})
+                   "l2": "working set about 50 MB (below L2); the timed steps run back to back"},
+                  chain_kernels=REBUILD_KERNELS + 1)
     h.destroy()
 
 

@@ -387,6 +387,22 @@ __global__ void k_reorder(Bufs b)
     }
 }
 
+// Slots of the bond partners and of the members of the angle triples, per
+// entry of the (particle-id ordered) bond and triple tables.  Slots change
+// only when the particles are re-sorted, so this runs once per rebuild and
+// the force kernel reads one entry per bond or triple instead of mapping
+// particle ids to slots every step.
+__global__ void k_topology_slots(Bufs b)
+{
+    if (!b.ctl->rebuild || b.ctl->err) return;
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < b.n_bond_ent) b.bond_pslot[q] = b.slot_of_id[b.bond_partner[q]];
+    if (q < b.n_ang_ent) {
+        const int4 e = b.ang_ent[q];
+        b.ang_slot[q] = make_int4(b.slot_of_id[e.x], b.slot_of_id[e.y], b.slot_of_id[e.z], e.w);
+    }
+}
+
 // ---------------------------------------------------------------- tiles
 // Rows of all replica grids are numbered replica by replica, cz-major; a warp
 // walks one row.  Lanes first sum, for every column x of the row, the
@@ -1042,6 +1058,8 @@ void launch_rebuild_chain(const Bufs &b, cudaStream_t st)
     k_scan_write<<<nsb, kScanBlock, 0, st>>>(b);
     k_scatter<<<b.nblk, kBlock, 0, st>>>(b);
     k_reorder<<<blocks_for((long long)b.C * 32, 256), 256, 0, st>>>(b);
+    const long long nt = b.n_bond_ent > b.n_ang_ent ? b.n_bond_ent : b.n_ang_ent;
+    if (nt > 0) k_topology_slots<<<blocks_for(nt, 256), 256, 0, st>>>(b);
     k_tile_count<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
     k_tile_scan<<<1, kScanThreads, 0, st>>>(b);
     k_tile_write<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);

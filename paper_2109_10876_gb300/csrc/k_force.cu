@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             if (b.has_bonds) {
                 const int id = (int)pi.w;
                 for (int q = b.bond_off[id]; q < b.bond_off[id + 1]; ++q) {
-                    const int sj = b.slot_of_id[b.bond_partner[q]];
+                    const int sj = b.bond_pslot[q];
                     if (PREC == 1) {
                         const uint4 pj = P[sj];
                         const float dx = (float)(int)(pi.x - pj.x) * R.qs[0];
@@ -852,8 +852,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             if (b.has_angles) {
                 const int id = (int)pi.w;
                 for (int q = b.ang_off[id]; q < b.ang_off[id + 1]; ++q) {
-                    const int4 e = b.ang_ent[q];
-                    const int sa = b.slot_of_id[e.x], sb = b.slot_of_id[e.y], sc = b.slot_of_id[e.z];
+                    const int4 e = b.ang_slot[q];      // slots of (a, b, c), role in .w
+                    const int sa = e.x, sb = e.y, sc = e.z;
                     if (PREC == 1) {
                         const uint4 pa = P[sa], pb = P[sb], pcc = P[sc];
                         const float b1[3] = {(float)(int)(pb.x - pa.x) * R.qs[0], (float)(int)(pb.y - pa.y) * R.qs[1],

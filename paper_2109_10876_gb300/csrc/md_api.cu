@@ -581,6 +581,8 @@ md_status md_create(const md_params *p, md_handle **out)
         ok &= cudaMemcpy(doff, deg.data(), sizeof(int) * (h->N + 1), cudaMemcpyHostToDevice) == cudaSuccess;
         ok &= cudaMemcpy(dpart, partner.data(), sizeof(int) * partner.size(), cudaMemcpyHostToDevice) == cudaSuccess;
         b.bond_off = doff;
+        b.n_bond_ent = (long long)partner.size();
+        if (!(b.bond_pslot = dalloc<int>(h, partner.size()))) { md_destroy(h); return MD_ERR_CUDA; }
         b.bond_partner = dpart;
         b.has_bonds = 1;
     }
@@ -604,6 +606,8 @@ md_status md_create(const md_params *p, md_handle **out)
         ok &= cudaMemcpy(dent, ent.data(), sizeof(int4) * ent.size(), cudaMemcpyHostToDevice) == cudaSuccess;
         b.ang_off = doff;
         b.ang_ent = dent;
+        b.n_ang_ent = (long long)ent.size();
+        if (!(b.ang_slot = dalloc<int4>(h, ent.size()))) { md_destroy(h); return MD_ERR_CUDA; }
         b.has_angles = 1;
         b.angle_K = p->angle_K;
         b.angle_K_f = (float)p->angle_K;
