@@ -85,7 +85,8 @@ typedef struct {
     double fene_K, fene_R0;         /* FENE bond constants                      */
     int64_t n_bonds;                /* FENE bonds                               */
     const int32_t *bonds;           /* 2 * n_bonds particle indices, or NULL    */
-    int32_t list_capacity;          /* neighbours per particle; 0 = automatic   */
+    int32_t list_capacity;          /* neighbours per particle, rounded up to a
+                                       multiple of 32; 0 = automatic            */
     int32_t reserved0;
     double angle_K;                 /* bending constant of the angle term       */
     int64_t n_angles;               /* angle triples                            */

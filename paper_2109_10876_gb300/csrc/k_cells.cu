@@ -68,6 +68,7 @@ __global__ void k_reset_ctl(Ctl *ctl)
     ctl->disp2_bits = 0u;
     ctl->err = 0;
     ctl->done_force = ctl->done_list = ctl->done_kick = 0u;
+    ctl->tile_next = 0u;
     ctl->max_occ = ctl->max_nn = 0;
     ctl->step = 0;
     ctl->rebuilds = 0;

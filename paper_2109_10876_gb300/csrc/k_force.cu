@@ -653,7 +653,13 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     __shared__ double sm3[kBlock / 32][3];
     __shared__ long long sml[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
+    __shared__ __align__(8) unsigned long long s_mbar;   // completion of a tile's bulk copies
     if (block_uniform(b.ctl->err != 0)) return;
+    // FP32 full-list tiles are staged by bulk (TMA) copies: thread 0 arms the
+    // barrier and copies the halo pieces and the list block, all threads wait
+    constexpr bool kBulk = (PREC == 1 && !HALF);
+    unsigned phase = 0;
+    if (kBulk && threadIdx.x == 0) mbar_init(&s_mbar, 1);
     const int cur = b.ctl->cur, nxt = cur ^ 1;
     const long long step = b.ctl->step;
     const double *X = b.x[cur];
@@ -689,14 +695,27 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             if (own_staged)
                 for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
             if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
-            if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
+            if (kBulk) {
+                if (threadIdx.x == 0) {
+                    // every piece is a contiguous run of 16-byte positions; the
+                    // list block starts 64-byte aligned and is read rounded up
+                    // to 16 bytes (the list and the stage carry that slack)
+                    const unsigned lbytes = tl.kmax * Pt <= kListStage * kTileMax
+                                                ? ((unsigned)(tl.kmax * Pt) * 2u + 15u) & ~15u : 0u;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&s_mbar, (unsigned)pc[np].hoff * 16u + lbytes);
+                    for (int q = 0; q < np; ++q)
+                        if (pc[q].n > 0) bulk_g2s(&hpos[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, &s_mbar);
+                    if (lbytes) bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, &s_mbar);
+                }
+            } else if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
             else stage_halo<double>(pc, np, [&](int h, int j) {
                 cp_async8(&hx[h], &X[j]);
                 cp_async8(&hy[h], &X[b.S + j]);
                 cp_async8(&hz[h], &X[2 * b.S + j]);
             });
             // the tile's lists: kmax rows of Pt entries, one contiguous block
-            if (tl.kmax * Pt <= kListStage * kTileMax) {
+            if (!kBulk && tl.kmax * Pt <= kListStage * kTileMax) {
                 const unsigned short *src = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0);
                 const int total = tl.kmax * Pt;            // entries; the block starts 64-byte aligned
                 const int nvec = total >> 3;
@@ -707,7 +726,15 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             }
             cp_async_wait_all();
         }
-        __syncthreads();
+        bool late = false;
+        if (kBulk) {
+            late = !mbar_wait(&s_mbar, phase);
+            phase ^= 1u;
+        }
+        if (__syncthreads_or(late)) {   // a bulk copy never completed: stop, report
+            err |= kErrTimeout;
+            break;
+        }
         const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
         double ui = 0.0, wi = 0.0, ki = 0.0;
         // FP32 path: energies as integers, twice the energy in units of 2^-22
@@ -1111,9 +1138,10 @@ static int persistent_grid(const void *fn, int block, size_t smem)
 template <int PREC, int MODE, bool ENERGY, bool HALF>
 static void launch_one(const Bufs &b, cudaStream_t st)
 {
+    // (16 bytes of slack: the bulk copy of a list block rounds up to 16 bytes)
     const size_t smem = HALF ? 0
                              : (size_t)b.hcap * (PREC == 1 ? sizeof(uint4) : 3 * sizeof(double)) +
-                                   (size_t)kListStage * kTileMax * sizeof(unsigned short);
+                                   (size_t)kListStage * kTileMax * sizeof(unsigned short) + 16;
     static int grid = 0;
     static size_t grid_smem = 0;
     if (grid == 0 || grid_smem != smem) {

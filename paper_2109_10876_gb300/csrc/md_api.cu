@@ -127,7 +127,9 @@ md_status alloc_list(md_handle *h, int K)
     h->K = K;
     h->b.K = K;
     h->gen++;
-    h->b.nbr = dalloc<unsigned short>(h, (size_t)K * (size_t)h->S);
+    // 16 entries of slack: the force kernel's bulk copy of a tile's list block
+    // rounds its length up to 16 bytes
+    h->b.nbr = dalloc<unsigned short>(h, (size_t)K * (size_t)h->S + 16);
     if (!h->b.nbr) return fail(h, MD_ERR_CUDA, "cannot allocate the neighbour list");
     return MD_OK;
 }
@@ -459,7 +461,11 @@ md_status md_create(const md_params *p, md_handle **out)
 
     // list capacity: 1.5x the ideal-gas count in the list sphere at the
     // densest replica, plus a margin (grown on overflow by md_build_neighbors)
-    int K = p->list_capacity;
+    if (p->list_capacity < 0) { delete h; return MD_ERR_ARG; }
+    // a given capacity is rounded up to a multiple of 32 entries, like the
+    // automatic one: every tile's list block then starts 64-byte aligned, as
+    // the 16-byte copies of the list kernels require
+    int K = (int)round_up(p->list_capacity, 32);
     h->auto_capacity = (K == 0);
     if (K == 0) {
         double kmax = 0;

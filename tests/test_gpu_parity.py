@@ -209,6 +209,23 @@ def test_list_overflow_is_reported(md):
     assert e.value.status == md.MD_ERR_LIST_OVERFLOW
 
 
+def test_given_capacity_is_rounded_up(md):
+    """A list capacity that is not a multiple of 32 (here 90) is rounded up
+    to one (96), so every tile's list block stays aligned for the 16-byte
+    copies; the pair set is exact."""
+    x, v, box = inputs.lj_fluid(10, seed=1)
+    h = md.md_create(len(x), box, list_capacity=90)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    assert md.md_get_stats(h)["list_capacity"] == 96
+    want, _ = oracle.pairs(oracle.System(len(x), box, rc=RC), x, RC + SKIN)
+    np.testing.assert_array_equal(md.export_pairs_sorted(h), want)
+    f = torch.zeros(3, len(x), dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, None)
+    md.md_step(h, 20)
+    md.md_sync(h)
+
+
 def test_automatic_capacity_grows(md):
     """A dense clump in a dilute box overflows the density-based capacity
     estimate; md_build_neighbors grows the list and the pair set is exact."""
