@@ -862,7 +862,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
+__global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
 {
     if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     extern __shared__ uint4 halo[];
@@ -872,6 +872,8 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
     __shared__ Tile tl;
     __shared__ int s_tile, s_np, s_kmax;
     __shared__ int s_rng[kBlock / 32][2][kMaxPieces][3];   // per warp: the ranges of both half-warp unions
+    __shared__ __align__(8) unsigned long long s_mbar;     // completion of a tile's halo copies
+    unsigned phase = 0;
     const int src = b.ctl->cur ^ 1;          // k_reorder wrote the sorted state here
     const uint4 *P = b.pos[src];
     const double *X = b.x[src];
@@ -879,7 +881,10 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
     int mx = 0;
     long long sm = 0;
     int err = 0;
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+    if (threadIdx.x == 0) {
+        s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        mbar_init(&s_mbar, 1);
+    }
     __syncthreads();
     for (;;) {
         const int t = s_tile;
@@ -900,9 +905,20 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Bufs b)
             __syncthreads();
             continue;
         }
-        stage_halo<uint4>(pc, s_np, [&](int h, int j) { cp_async16(&halo[h], &P[j]); });
-        cp_async_wait_all();
-        __syncthreads();
+        // the halo pieces (contiguous runs of 16-byte positions) by bulk (TMA)
+        // copies issued by one thread; every thread waits on the barrier
+        if (threadIdx.x == 0) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&s_mbar, (unsigned)H * 16u);
+            for (int q = 0; q < s_np; ++q)
+                if (pc[q].n > 0) bulk_g2s(&halo[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, &s_mbar);
+        }
+        const bool late = !mbar_wait(&s_mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(late)) {   // a bulk copy never completed: stop, report
+            err |= kErrTimeout;
+            break;
+        }
         const bool rel = R.ncell[1] >= 3 && R.ncell[2] >= 3 && tl.x1 - tl.x0 <= R.ncell[0] - 3;
         if (rel) {
             // FP32 coordinates relative to the tile centre (exact integer
