@@ -646,9 +646,12 @@ template <int PREC, int MODE, bool ENERGY, bool HALF = false>
 __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) k_force(Bufs b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Piece pc[kMaxPieces + 1];
-    __shared__ Tile tl;
-    __shared__ int s_tile, s_np, s_self;
+    // tile records and halo pieces, double-buffered: the next tile's are
+    // copied in by one warp while this one is computed
+    __shared__ Piece pcb[2][kMaxPieces + 1];
+    __shared__ Tile tlb[2];
+    __shared__ int s_npb[2];
+    __shared__ int s_tile, s_self, s_next;
     __shared__ int s_nn[kTileMax];
     __shared__ double sm3[kBlock / 32][3];
     __shared__ long long sml[kBlock / 32][3];
@@ -670,6 +673,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     unsigned short *lst = reinterpret_cast<unsigned short *>(smem_raw + (size_t)b.hcap * (PREC == 1 ? sizeof(uint4) : 3 * sizeof(double)));
     float ratio = 0.0f;
     int err = 0;
+    int buf = 0;           // which tile buffer holds tile t
+    bool have = false;     // whether it was prefetched
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
     __syncthreads();
     for (;;) {
@@ -679,15 +684,18 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         // the next tile is claimed now and published at the end of this one
         int t_next = 0;
         if (threadIdx.x == 0) t_next = (int)atomicAdd(&b.ctl->tile_next, 1u);
-        load_tile(b, t, tl, pc, s_np);
+        if (!have) load_tile(b, t, tlb[buf], pcb[buf], s_npb[buf]);
         __syncthreads();
+        Piece *const pc = pcb[buf];
+        const Tile &tl = tlb[buf];
         const Replica &R = b.rep[tl.rep];
-        const int np = s_np;
+        const int np = s_npb[buf];
         const int Pt = tl.s1 - tl.s0;
         if (!HALF && pc[np].hoff > b.hcap) {          // the list build rejects such tiles first
             err |= kErrList;
             if (threadIdx.x == 0) s_tile = t_next;
             __syncthreads();
+            have = false;
             continue;
         }
         const bool own_staged = Pt <= kTileMax;
@@ -726,6 +734,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             }
             cp_async_wait_all();
         }
+        if (threadIdx.x == 0) s_next = t_next;
         bool late = false;
         if (kBulk) {
             late = !mbar_wait(&s_mbar, phase);
@@ -735,6 +744,12 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             err |= kErrTimeout;
             break;
         }
+        // the last warp copies the next tile's record and pieces into the other
+        // buffer while the tile is computed
+        const int tn = s_next;
+        const bool pref = tn < b.ctl->ntiles;
+        if (pref && threadIdx.x >= blockDim.x - 32)
+            prefetch_tile_async(b, tn, tlb[buf ^ 1], pcb[buf ^ 1], s_npb[buf ^ 1], threadIdx.x & 31);
         const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
         double ui = 0.0, wi = 0.0, ki = 0.0;
         // FP32 path: energies as integers, twice the energy in units of 2^-22
@@ -990,8 +1005,11 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 b.partial[4 * t + 2] = d;
             }
         }
+        cp_async_wait_all();   // the next tile's record (the copying warp)
         if (threadIdx.x == 0) s_tile = t_next;
         __syncthreads();   // the halo and the tile record are reused by the next tile
+        buf ^= 1;
+        have = pref;
     }
     if (err) atomicOr(&b.ctl->err, err);
     constexpr bool kDrift = (MODE == kModeFused);

@@ -318,6 +318,21 @@ __device__ __forceinline__ void load_tile(const Bufs &b, int t, Tile &tl, Piece 
     for (int m = threadIdx.x; m < words; m += blockDim.x) dst[m] = src[m];
 }
 
+// The same record and pieces, copied asynchronously by the 32 lanes of one
+// warp (completion: cp_async_wait_all by those lanes, then a block barrier).
+__device__ __forceinline__ void prefetch_tile_async(const Bufs &b, int t, Tile &tl, Piece *pc, int &np, int lane)
+{
+    const int *src = reinterpret_cast<const int *>(b.pieces + (size_t)t * (kMaxPieces + 1));
+    int *dst = reinterpret_cast<int *>(pc);
+    constexpr int words = (kMaxPieces + 1) * sizeof(Piece) / sizeof(int);
+    for (int m = lane; m < words; m += 32) cp_async4(dst + m, src + m);
+    const int *ts = reinterpret_cast<const int *>(b.tiles + t);
+    int *td = reinterpret_cast<int *>(&tl);
+    constexpr int tw = sizeof(Tile) / sizeof(int);
+    for (int m = lane; m < tw; m += 32) cp_async4(td + m, ts + m);
+    if (lane == 0) cp_async4(&np, b.tile_np + t);
+}
+
 // A decision taken by thread 0 and shared with the whole block, so that every
 // thread of a block takes the same early return: an error latched by another
 // block while this one starts cannot split it across its barriers.
