@@ -35,25 +35,22 @@ __device__ __forceinline__ int adj_halo_slot(const Piece *pc, int np, int h)
     return pc[q].slot0 + (h - pc[q].hoff);
 }
 
-// Last block: per-replica sums of the 4 per-tile partials, in tile order,
-// added into acc[4 * r + k] with weight `scale`.
+// Last block: per-replica sums of the 4 per-tile partials, added into
+// acc[4 * r + k] with weight `scale`.  Each warp takes every fourth replica:
+// lane-strided sums over its tiles, then a shuffle tree (a fixed order, so
+// the result does not depend on timing); no block barriers.
 __device__ void adj_reduce(const Bufs &b, double scale, double *acc)
 {
-    __shared__ double red[kBlock][4];
-    for (int r = 0; r < b.nrep; ++r) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int r = warp; r < b.nrep; r += nwarp) {
         double a[4] = {0, 0, 0, 0};
-        for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x)
+        for (int q = b.rep_tile[r] + lane; q < b.rep_tile[r + 1]; q += 32)
             for (int k = 0; k < 4; ++k) a[k] += b.partial[4 * q + k];
-        for (int k = 0; k < 4; ++k) red[threadIdx.x][k] = a[k];
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s)
-                for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 4; ++k) acc[4 * r + k] += scale * red[0][k];
-        __syncthreads();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < 4; ++k) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+        if (lane == 0)
+            for (int k = 0; k < 4; ++k) acc[4 * r + k] += scale * a[k];
     }
 }
 
@@ -197,6 +194,34 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
     }
 }
 
+// Reciprocal by the hardware approximation (a pure function of its input).
+__device__ __forceinline__ float rcp_approx_f(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// w (caller order, FP64) into slot order as FP32 (hi, lo) pieces, so that the
+// halo staging of k_adj_hvp32 copies contiguous runs instead of gathering and
+// converting w for every halo entry.
+__global__ void k_adj_wslots(Bufs b, const double *w)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.S) return;
+    const int id = (int)b.pos[b.ctl->cur][s].w;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 c = make_float2(0.f, 0.f);
+    if (id >= 0) {
+        const double w0 = w[id], w1 = w[b.N + id], w2 = w[2 * b.N + id];
+        const float a0 = (float)w0, a1 = (float)w1, a2 = (float)w2;
+        a = make_float4(a0, a1, a2, (float)(w0 - (double)a0));
+        c = make_float2((float)(w1 - (double)a1), (float)(w2 - (double)a2));
+    }
+    b.adj_wa[s] = a;
+    b.adj_wb[s] = c;
+}
+
 // Hessian-vector product for the FP32 + fixed-point forward path (MODE 0 of
 // k_adj in FP32): separations from the fixed-point positions as in the force
 // kernel, the interacting set decided the same way (FP64 within rounding of
@@ -229,18 +254,16 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
         const int np = s_np;
         const int Pt = tl.s1 - tl.s0;
         stage_halo<uint4>(pc, np, [&](int h, int j) {
-            const uint4 q = P[j];
-            hpos[h] = q;
-            const int id = (int)q.w;
-            const double w0 = w[id], w1 = w[b.N + id], w2 = w[2 * b.N + id];
-            const float a0 = (float)w0, a1 = (float)w1, a2 = (float)w2;
-            hwa[h] = make_float4(a0, a1, a2, (float)(w0 - (double)a0));
-            hwb[h] = make_float2((float)(w1 - (double)a1), (float)(w2 - (double)a2));
+            cp_async16(&hpos[h], &P[j]);
+            cp_async16(&hwa[h], &b.adj_wa[j]);
+            cp_async8(&hwb[h], &b.adj_wb[j]);
         });
+        cp_async_wait_all();
         __syncthreads();
         const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
         const float lo = R.rc2_lo, hi = R.rc2_hi;
         const float eps24 = 24.0f * (float)R.eps, sig2 = (float)(R.sigma * R.sigma), isig = (float)(1.0 / R.sigma);
+        const double ieps = 1.0 / R.eps;
         double p0 = 0.0, p1 = 0.0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
             const uint4 pi = P[i];
@@ -248,39 +271,50 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
             const int n = min(b.nn[i], b.K);
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
             const double wi0 = w[id], wi1 = w[b.N + id], wi2 = w[2 * b.N + id];
-            const float ah0 = (float)wi0, ah1 = (float)wi1, ah2 = (float)wi2;
-            const float al0 = (float)(wi0 - (double)ah0), al1 = (float)(wi1 - (double)ah1), al2 = (float)(wi2 - (double)ah2);
+            const float4 wai = b.adj_wa[i];
+            const float2 wbi = b.adj_wb[i];
+            const float ah0 = wai.x, ah1 = wai.y, ah2 = wai.z;
+            const float al0 = wai.w, al1 = wbi.x, al2 = wbi.y;
             float acc3[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f}, Fs[3] = {0.f, 0.f, 0.f};
-            for (int k = 0; k < n; ++k) {
-                const int h = __ldg(nb + (long long)k * Pt);
-                const uint4 pj = hpos[h];
-                const float dx = (float)(int)(pi.x - pj.x) * qs0;
-                const float dy = (float)(int)(pi.y - pj.y) * qs1;
-                const float dz = (float)(int)(pi.z - pj.z) * qs2;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (!(r2 < hi)) continue;
-                if (!(r2 < lo) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < R.rc2)) continue;
-                const float ir2 = 1.0f / r2;
-                const float s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
-                const float e24 = eps24 * ir2;
-                const float g = e24 * (2.0f * s12 - s6);
-                const float gpr = e24 * ir2 * (8.0f * s6 - 28.0f * s12);
-                const float dgds = e24 * isig * (24.0f * s12 - 6.0f * s6);
-                const float4 wa = hwa[h];
-                const float2 wb = hwb[h];
-                const float dw0 = (ah0 - wa.x) + (al0 - wa.w);
-                const float dw1 = (ah1 - wa.y) + (al1 - wb.x);
-                const float dw2 = (ah2 - wa.z) + (al2 - wb.y);
-                const float ddw = dx * dw0 + dy * dw1 + dz * dw2;
-                const float gd = gpr * ddw;
-                acc3[0] += g * dw0 + gd * dx;
-                acc3[1] += g * dw1 + gd * dy;
-                acc3[2] += g * dw2 + gd * dz;
-                F[0] += g * dx; F[1] += g * dy; F[2] += g * dz;
-                Fs[0] += dgds * dx; Fs[1] += dgds * dy; Fs[2] += dgds * dz;
+            // four list entries in flight at a time (the list is read from
+            // global memory; its latency, not the arithmetic, sets the pace)
+            for (int k0 = 0; k0 < n; k0 += 4) {
+                int hh[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) hh[u] = k0 + u < n ? (int)__ldg(nb + (long long)(k0 + u) * Pt) : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int h = hh[u];
+                    if (h < 0) continue;
+                    const uint4 pj = hpos[h];
+                    const float dx = (float)(int)(pi.x - pj.x) * qs0;
+                    const float dy = (float)(int)(pi.y - pj.y) * qs1;
+                    const float dz = (float)(int)(pi.z - pj.z) * qs2;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (!(r2 < hi)) continue;
+                    if (!(r2 < lo) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < R.rc2)) continue;
+                    const float ir2 = rcp_approx_f(r2);
+                    const float s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
+                    const float e24 = eps24 * ir2;
+                    const float g = e24 * (2.0f * s12 - s6);
+                    const float gpr = e24 * ir2 * (8.0f * s6 - 28.0f * s12);
+                    const float dgds = e24 * isig * (24.0f * s12 - 6.0f * s6);
+                    const float4 wa = hwa[h];
+                    const float2 wb = hwb[h];
+                    const float dw0 = (ah0 - wa.x) + (al0 - wa.w);
+                    const float dw1 = (ah1 - wa.y) + (al1 - wb.x);
+                    const float dw2 = (ah2 - wa.z) + (al2 - wb.y);
+                    const float ddw = dx * dw0 + dy * dw1 + dz * dw2;
+                    const float gd = gpr * ddw;
+                    acc3[0] += g * dw0 + gd * dx;
+                    acc3[1] += g * dw1 + gd * dy;
+                    acc3[2] += g * dw2 + gd * dz;
+                    F[0] += g * dx; F[1] += g * dy; F[2] += g * dz;
+                    Fs[0] += dgds * dx; Fs[1] += dgds * dy; Fs[2] += dgds * dz;
+                }
             }
             for (int q = 0; q < 3; ++q) out[q * b.N + id] = (double)acc3[q];
-            p0 += (wi0 * F[0] + wi1 * F[1] + wi2 * F[2]) / R.eps;
+            p0 += (wi0 * F[0] + wi1 * F[1] + wi2 * F[2]) * ieps;
             p1 += wi0 * Fs[0] + wi1 * Fs[1] + wi2 * Fs[2];
         }
         // per-tile partials in a fixed order
@@ -357,6 +391,7 @@ void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, d
         static int grid32 = 0;
         static size_t gs32 = 0;
         if (grid32 == 0 || gs32 != smem32) { grid32 = adj_grid((const void *)k_adj_hvp32, smem32); gs32 = smem32; }
+        k_adj_wslots<<<(unsigned)((b.S + 255) / 256), 256, 0, st>>>(b, w);
         k_adj_hvp32<<<grid32, kBlock, smem32, st>>>(b, w, hv, scale, g);
         return;
     }

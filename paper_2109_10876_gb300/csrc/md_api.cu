@@ -915,6 +915,11 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
         h->ad_seg_cap = k + 1;
     }
     if (!h->ad_small && !(h->ad_small = dalloc<double>(h, (size_t)(12 * nrep)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    if (h->precision == MD_FP32_FIXED && !h->b.adj_wa) {
+        h->b.adj_wa = dalloc<float4>(h, (size_t)h->S);
+        h->b.adj_wb = dalloc<float2>(h, (size_t)h->S);
+        if (!h->b.adj_wa || !h->b.adj_wb) return fail(h, MD_ERR_CUDA, "cannot allocate");
+    }
     double *lx = h->ad_work, *lv = lx + n3, *hv = lv + n3;
     double *coef = h->ad_small, *g = coef + 4 * nrep, *sums = g + 4 * nrep;
     // loss weights (dL/dU, dL/dK, dL/dW) per replica, from host or device memory

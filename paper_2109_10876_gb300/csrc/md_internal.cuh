@@ -203,6 +203,8 @@ struct Bufs {
     const int *bond_partner; // 2 * n_bonds particle ids
     const int *ang_off;      // N + 1: angle entries of particle id
     const int4 *ang_ent;     // 3 * n_angles: (a, b, c, role of the particle: 0, 1, 2)
+    float4 *adj_wa;          // reverse pass: w by slot as FP32 pieces (hi x, hi y, hi z, lo x), S entries
+    float2 *adj_wb;          // (lo y, lo z), S entries
     int *bond_pslot;         // 2 * n_bonds: current slot of each bond_partner entry (refreshed per re-sort)
     int4 *ang_slot;          // 3 * n_angles: current slots of (a, b, c) and the role, per ang_ent entry
     long long n_bond_ent, n_ang_ent;
