@@ -276,14 +276,14 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
             const float ah0 = wai.x, ah1 = wai.y, ah2 = wai.z;
             const float al0 = wai.w, al1 = wbi.x, al2 = wbi.y;
             float acc3[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f}, Fs[3] = {0.f, 0.f, 0.f};
-            // four list entries in flight at a time (the list is read from
+            // eight list entries in flight at a time (the list is read from
             // global memory; its latency, not the arithmetic, sets the pace)
-            for (int k0 = 0; k0 < n; k0 += 4) {
-                int hh[4];
+            for (int k0 = 0; k0 < n; k0 += 8) {
+                int hh[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) hh[u] = k0 + u < n ? (int)__ldg(nb + (long long)(k0 + u) * Pt) : -1;
+                for (int u = 0; u < 8; ++u) hh[u] = k0 + u < n ? (int)__ldg(nb + (long long)(k0 + u) * Pt) : -1;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 8; ++u) {
                     const int h = hh[u];
                     if (h < 0) continue;
                     const uint4 pj = hpos[h];
