@@ -241,8 +241,6 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
     const double *X = b.x[cur];
     const uint4 *P = b.pos[cur];
     uint4 *hpos = reinterpret_cast<uint4 *>(smem_raw);
-    float4 *hwa = reinterpret_cast<float4 *>(hpos + b.hcap);   // (hi x, hi y, hi z, lo x)
-    float2 *hwb = reinterpret_cast<float2 *>(hwa + b.hcap);    // (lo y, lo z)
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
         __syncthreads();
@@ -253,12 +251,12 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
         const Replica &R = b.rep[tl.rep];
         const int np = s_np;
         const int Pt = tl.s1 - tl.s0;
-        stage_halo<uint4>(pc, np, [&](int h, int j) {
-            cp_async16(&hpos[h], &P[j]);
-            cp_async16(&hwa[h], &b.adj_wa[j]);
-            cp_async8(&hwb[h], &b.adj_wb[j]);
-        });
+        // positions only (the halo's w is read by slot from the slot-ordered
+        // table, which stays in L1 for the tile); the fourth word becomes the slot
+        stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
         cp_async_wait_all();
+        __syncthreads();
+        stage_halo<uint4>(pc, np, [&](int h, int j) { hpos[h].w = (unsigned)j; });
         __syncthreads();
         const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
         const float lo = R.rc2_lo, hi = R.rc2_hi;
@@ -299,8 +297,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
                     const float g = e24 * (2.0f * s12 - s6);
                     const float gpr = e24 * ir2 * (8.0f * s6 - 28.0f * s12);
                     const float dgds = e24 * isig * (24.0f * s12 - 6.0f * s6);
-                    const float4 wa = hwa[h];
-                    const float2 wb = hwb[h];
+                    const float4 wa = __ldg(b.adj_wa + pj.w);
+                    const float2 wb = __ldg(b.adj_wb + pj.w);
                     const float dw0 = (ah0 - wa.x) + (al0 - wa.w);
                     const float dw1 = (ah1 - wa.y) + (al1 - wb.x);
                     const float dw2 = (ah2 - wa.z) + (al2 - wb.y);
@@ -387,7 +385,7 @@ void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, d
                     cudaStream_t st)
 {
     if (precision == 1) {
-        const size_t smem32 = (size_t)b.hcap * (sizeof(uint4) + sizeof(float4) + sizeof(float2));
+        const size_t smem32 = (size_t)b.hcap * sizeof(uint4);
         static int grid32 = 0;
         static size_t gs32 = 0;
         if (grid32 == 0 || gs32 != smem32) { grid32 = adj_grid((const void *)k_adj_hvp32, smem32); gs32 = smem32; }
