@@ -638,6 +638,22 @@ __device__ __forceinline__ void angle_term(const Real b1[3], const Real b2[3], R
 // the neighbour positions read from the tile's halo in shared memory, then
 // the velocity-Verlet update of that particle.  Persistent blocks take tiles
 // from a work counter.
+// Thread 0 arms the staging barrier with the tile's byte count and issues
+// its bulk (TMA) copies: the halo pieces (contiguous runs of 16-byte
+// positions) and, if it fits the stage, the list block (64-byte aligned, read
+// rounded up to 16 bytes; the list and the stage carry that slack).
+__device__ __forceinline__ void issue_tile_bulk(const Bufs &b, const Tile &tl, const Piece *pc, int np, const uint4 *P,
+                                                uint4 *hpos, unsigned short *lst, unsigned long long *bar)
+{
+    const int Pt = tl.s1 - tl.s0;
+    const unsigned lbytes = tl.kmax * Pt <= kListStage * kTileMax ? ((unsigned)(tl.kmax * Pt) * 2u + 15u) & ~15u : 0u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u + lbytes);
+    for (int q = 0; q < np; ++q)
+        if (pc[q].n > 0) bulk_g2s(&hpos[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, bar);
+    if (lbytes) bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, bar);
+}
+
 // HALF (FP32 only): the second kernel of a half-list step.  k_pairs_half has
 // left each particle's total pair force in the fixed-point sums Fq; this pass
 // takes it from there (and clears it) instead of walking a list, then does
@@ -651,7 +667,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     __shared__ Piece pcb[2][kMaxPieces + 1];
     __shared__ Tile tlb[2];
     __shared__ int s_npb[2];
-    __shared__ int s_tile, s_self, s_next;
+    __shared__ int s_tile, s_self, s_next, s_issued;
     __shared__ int s_nn[kTileMax];
     __shared__ double sm3[kBlock / 32][3];
     __shared__ long long sml[kBlock / 32][3];
@@ -675,10 +691,14 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     int err = 0;
     int buf = 0;           // which tile buffer holds tile t
     bool have = false;     // whether it was prefetched
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+    if (threadIdx.x == 0) {
+        s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        s_issued = 0;
+    }
     __syncthreads();
     for (;;) {
         const int t = s_tile;
+        const bool issued = s_issued != 0;   // this tile's copies went out during the last one
         __syncthreads();
         if (t >= b.ctl->ntiles) break;
         // the next tile is claimed now and published at the end of this one
@@ -693,7 +713,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         const int Pt = tl.s1 - tl.s0;
         if (!HALF && pc[np].hoff > b.hcap) {          // the list build rejects such tiles first
             err |= kErrList;
-            if (threadIdx.x == 0) s_tile = t_next;
+            if (threadIdx.x == 0) { s_tile = t_next; s_issued = 0; }
             __syncthreads();
             have = false;
             continue;
@@ -704,18 +724,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
             if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
             if (kBulk) {
-                if (threadIdx.x == 0) {
-                    // every piece is a contiguous run of 16-byte positions; the
-                    // list block starts 64-byte aligned and is read rounded up
-                    // to 16 bytes (the list and the stage carry that slack)
-                    const unsigned lbytes = tl.kmax * Pt <= kListStage * kTileMax
-                                                ? ((unsigned)(tl.kmax * Pt) * 2u + 15u) & ~15u : 0u;
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&s_mbar, (unsigned)pc[np].hoff * 16u + lbytes);
-                    for (int q = 0; q < np; ++q)
-                        if (pc[q].n > 0) bulk_g2s(&hpos[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, &s_mbar);
-                    if (lbytes) bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, &s_mbar);
-                }
+                if (threadIdx.x == 0 && !issued) issue_tile_bulk(b, tl, pc, np, P, hpos, lst, &s_mbar);
             } else if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
             else stage_halo<double>(pc, np, [&](int h, int j) {
                 cp_async8(&hx[h], &X[j]);
@@ -754,20 +763,32 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         double ui = 0.0, wi = 0.0, ki = 0.0;
         // FP32 path: energies as integers, twice the energy in units of 2^-22
         long long uf = 0, wf = 0, kf = 0;
-        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+        // Per particle: the pair sums (phase 1, which reads the staged halo
+        // and list) and everything after them (phase 2: bonded terms, Langevin
+        // force, integration, energies), which reads neither.
+        struct PState {
+            uint4 pi;
+            double Fd[3];
+            double fscale, ckick;
+        };
+        auto phase1 = [&](long long i, PState &ps) {
             if (MODE == kModeFused) {
                 // this particle's integration state, needed after the pair loop
                 prefetch_l1(&b.v[cur][i]); prefetch_l1(&b.v[cur][b.S + i]); prefetch_l1(&b.v[cur][2 * b.S + i]);
                 prefetch_l1(&X[i]); prefetch_l1(&X[b.S + i]); prefetch_l1(&X[2 * b.S + i]);
                 prefetch_l1(&b.xref[i]);
             }
-            const uint4 pi = (PREC == 1 && !HALF) ? hpos[s_self + (int)(i - tl.s0)] : P[i];
+            ps.pi = (PREC == 1 && !HALF) ? hpos[s_self + (int)(i - tl.s0)] : P[i];
+            const uint4 pi = ps.pi;
             const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
             const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));   // entry k at nb[k Pt]
-            double Fd[3] = {0.0, 0.0, 0.0};
-            double fscale = 1.0;
-            double ckick = b.half_dt_over_m;     // half kick per unit of Fd
+            double *Fd = ps.Fd;
+            Fd[0] = Fd[1] = Fd[2] = 0.0;
+            double &fscale = ps.fscale;
+            fscale = 1.0;
+            double &ckick = ps.ckick;
+            ckick = b.half_dt_over_m;            // half kick per unit of Fd
             if (PREC == 1 && HALF) {
                 // the pair sums of k_pairs_half, cleared for the next step
 #pragma unroll
@@ -847,6 +868,12 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 }
                 if (!isfinite(Fd[0]) || !isfinite(Fd[1]) || !isfinite(Fd[2])) err |= kErrNonfinite;
             }
+        };
+        auto phase2 = [&](long long i, PState &ps) {
+            const uint4 pi = ps.pi;
+            double *Fd = ps.Fd;
+            double &fscale = ps.fscale;
+            double &ckick = ps.ckick;
             // FENE bonds of this particle (Sec. 4), both ends of every bond
             // visited; in FP32 mode the bond force joins the fixed-point sum
             if (b.has_bonds) {
@@ -982,6 +1009,31 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 }
                 ratio = fmaxf(ratio, drift(b, R, i, nxt, pi.w, xi, v));
             }
+        };
+        // With one particle per thread, the next tile's bulk copies go out as
+        // soon as every thread is past its pair sums and arrive during phase 2.
+        int issued_next = 0;   // thread 0
+        if (kBulk && Pt <= (int)blockDim.x) {
+            PState ps;
+            const long long i = tl.s0 + threadIdx.x;
+            const bool act = i < tl.s1;
+            if (act) phase1(i, ps);
+            cp_async_wait_all();   // the next tile's record (the copying warp)
+            __syncthreads();
+            if (threadIdx.x == 0 && pref) {
+                const int npn = s_npb[buf ^ 1];
+                if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
+                    issue_tile_bulk(b, tlb[buf ^ 1], pcb[buf ^ 1], npn, P, hpos, lst, &s_mbar);
+                    issued_next = 1;
+                }
+            }
+            if (act) phase2(i, ps);
+        } else {
+            for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+                PState ps;
+                phase1(i, ps);
+                phase2(i, ps);
+            }
         }
         if (ENERGY && PREC == 1) {
             block_sum3_ll(uf, kf, wf, sml);
@@ -1006,7 +1058,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             }
         }
         cp_async_wait_all();   // the next tile's record (the copying warp)
-        if (threadIdx.x == 0) s_tile = t_next;
+        if (threadIdx.x == 0) {
+            s_tile = t_next;
+            s_issued = issued_next;
+        }
         __syncthreads();   // the halo and the tile record are reused by the next tile
         buf ^= 1;
         have = pref;
