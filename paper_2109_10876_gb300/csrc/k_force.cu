@@ -673,12 +673,17 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     __shared__ long long sml[kBlock / 32][3];
     __shared__ float smr[kBlock / 32];
     __shared__ __align__(8) unsigned long long s_mbar;   // completion of a tile's bulk copies
+    __shared__ __align__(8) unsigned long long s_p1bar;  // every thread past its pair sums
     if (block_uniform(b.ctl->err != 0)) return;
     // FP32 full-list tiles are staged by bulk (TMA) copies: thread 0 arms the
     // barrier and copies the halo pieces and the list block, all threads wait
     constexpr bool kBulk = (PREC == 1 && !HALF);
     unsigned phase = 0;
-    if (kBulk && threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    unsigned p1phase = 0;
+    if (kBulk && threadIdx.x == 0) {
+        mbar_init(&s_mbar, 1);
+        mbar_init(&s_p1bar, blockDim.x);
+    }
     const int cur = b.ctl->cur, nxt = cur ^ 1;
     const long long step = b.ctl->step;
     const double *X = b.x[cur];
@@ -1011,7 +1016,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             }
         };
         // With one particle per thread, the next tile's bulk copies go out as
-        // soon as every thread is past its pair sums and arrive during phase 2.
+        // soon as every thread is past its pair sums and arrive during phase 2:
+        // each thread arrives on s_p1bar after phase 1 (the copying warp once its
+        // copies of the next tile's record are complete); only thread 0 waits
+        // for all of them, then issues.
         int issued_next = 0;   // thread 0
         if (kBulk && Pt <= (int)blockDim.x) {
             PState ps;
@@ -1019,14 +1027,18 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             const bool act = i < tl.s1;
             if (act) phase1(i, ps);
             cp_async_wait_all();   // the next tile's record (the copying warp)
-            __syncthreads();
-            if (threadIdx.x == 0 && pref) {
-                const int npn = s_npb[buf ^ 1];
-                if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
-                    issue_tile_bulk(b, tlb[buf ^ 1], pcb[buf ^ 1], npn, P, hpos, lst, &s_mbar);
-                    issued_next = 1;
+            mbar_arrive(&s_p1bar);
+            if (threadIdx.x == 0) {
+                if (!mbar_wait(&s_p1bar, p1phase)) err |= kErrTimeout;
+                else if (pref) {
+                    const int npn = s_npb[buf ^ 1];
+                    if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
+                        issue_tile_bulk(b, tlb[buf ^ 1], pcb[buf ^ 1], npn, P, hpos, lst, &s_mbar);
+                        issued_next = 1;
+                    }
                 }
             }
+            p1phase ^= 1u;
             if (act) phase2(i, ps);
         } else {
             for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {

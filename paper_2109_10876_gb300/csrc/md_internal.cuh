@@ -266,6 +266,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// a plain arrival (count 1, no bytes), release semantics at CTA scope
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // orders this thread's earlier generic-proxy accesses to shared memory before
 // its later bulk copies into it
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
