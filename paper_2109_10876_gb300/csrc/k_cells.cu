@@ -862,15 +862,31 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
     }
 }
 
+// Thread 0 arms the staging barrier with the halo's byte count and issues its
+// bulk (TMA) copies: the pieces, contiguous runs of 16-byte positions.
+__device__ __forceinline__ void issue_halo_bulk(const Piece *pc, int np, const uint4 *P, uint4 *halo,
+                                                unsigned long long *bar)
+{
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u);
+    for (int q = 0; q < np; ++q)
+        if (pc[q].n > 0) bulk_g2s(&halo[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, bar);
+}
+
 __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
 {
     if (block_uniform(!b.ctl->rebuild || b.ctl->err)) return;
     extern __shared__ uint4 halo[];
     float4 *halof = reinterpret_cast<float4 *>(halo);                          // the same entries, converted
     unsigned short *lst = reinterpret_cast<unsigned short *>(halo + b.hcap);   // [k][Pt] stage, then 32 dummy slots
-    __shared__ Piece pc[kMaxPieces + 1];
-    __shared__ Tile tl;
-    __shared__ int s_tile, s_np, s_kmax;
+    // tile records and halo pieces, double-buffered: the next tile's are
+    // copied in by one warp while this one is walked
+    __shared__ Piece pcb[2][kMaxPieces + 1];
+    __shared__ Tile tlb[2];
+    __shared__ int s_npb[2];
+    __shared__ int s_tile, s_kmax, s_next, s_issued;
+    int buf = 0;
+    bool have = false;
     __shared__ int s_rng[kBlock / 32][2][kMaxPieces][3];   // per warp: the ranges of both half-warp unions
     __shared__ __align__(8) unsigned long long s_mbar;     // completion of a tile's halo copies
     unsigned phase = 0;
@@ -883,35 +899,39 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
     int err = 0;
     if (threadIdx.x == 0) {
         s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
+        s_issued = 0;
         mbar_init(&s_mbar, 1);
     }
     __syncthreads();
     for (;;) {
         const int t = s_tile;
+        const bool issued = s_issued != 0;   // this tile's halo copies went out during the last one
         __syncthreads();
         if (t >= b.ctl->ntiles) break;
         // the next tile is claimed now and published at the end of this one
         int t_next = 0;
         if (threadIdx.x == 0) { t_next = (int)atomicAdd(&b.ctl->tile_next, 1u); s_kmax = 0; }
-        load_tile(b, t, tl, pc, s_np);
+        if (!have) load_tile(b, t, tlb[buf], pcb[buf], s_npb[buf]);
         __syncthreads();
+        const Piece *const pc = pcb[buf];
+        const Tile &tl = tlb[buf];
+        const int s_np = s_npb[buf];
         const Replica &R = b.rep[tl.rep];
         const int H = pc[s_np].hoff;
         const int Pt = tl.s1 - tl.s0;
         if (H > b.hcap) {
             err |= kErrList;                 // halo does not fit: the host grows hcap and rebuilds
             for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) b.nn[i] = 0;
-            if (threadIdx.x == 0) s_tile = t_next;
+            if (threadIdx.x == 0) { s_tile = t_next; s_issued = 0; }
             __syncthreads();
+            have = false;
             continue;
         }
         // the halo pieces (contiguous runs of 16-byte positions) by bulk (TMA)
         // copies issued by one thread; every thread waits on the barrier
         if (threadIdx.x == 0) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&s_mbar, (unsigned)H * 16u);
-            for (int q = 0; q < s_np; ++q)
-                if (pc[q].n > 0) bulk_g2s(&halo[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, &s_mbar);
+            s_next = t_next;
+            if (!issued) issue_halo_bulk(pc, s_np, P, halo, &s_mbar);
         }
         const bool late = !mbar_wait(&s_mbar, phase);
         phase ^= 1u;
@@ -919,6 +939,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
             err |= kErrTimeout;
             break;
         }
+        // the last warp copies the next tile's record and pieces into the other
+        // buffer while this one is walked
+        const int tn = s_next;
+        const bool pref = tn < b.ctl->ntiles;
+        if (pref && threadIdx.x >= blockDim.x - 32)
+            prefetch_tile_async(b, tn, tlb[buf ^ 1], pcb[buf ^ 1], s_npb[buf ^ 1], threadIdx.x & 31);
         const bool rel = R.ncell[1] >= 3 && R.ncell[2] >= 3 && tl.x1 - tl.x0 <= R.ncell[0] - 3;
         if (rel) {
             // FP32 coordinates relative to the tile centre (exact integer
@@ -941,8 +967,21 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
             if (rel) cells_of_tile<true, false>(b, R, tl, pc, s_np, halof, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
             else cells_of_tile<false, false>(b, R, tl, pc, s_np, halo, lst, X, hfirst, s_rng[warp], &s_kmax, mx, sm, err);
         }
+        cp_async_wait_all();   // the next tile's record (the copying warp)
         __syncthreads();
-        if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;
+        // the halo is free: the next tile's halo copies go out now and arrive
+        // while this tile's lists are copied out
+        int issued_next = 0;   // thread 0
+        if (threadIdx.x == 0) {
+            b.tiles[t].kmax = s_kmax;
+            if (pref) {
+                const int npn = s_npb[buf ^ 1];
+                if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
+                    issue_halo_bulk(pcb[buf ^ 1], npn, P, halo, &s_mbar);
+                    issued_next = 1;
+                }
+            }
+        }
         // the staged rows are the start of the tile's list block: one
         // contiguous copy (the block starts 64-byte aligned)
         const int cap = Pt <= kTileMax ? min((kListStage * kTileMax) / max(Pt, 1), b.K) : 0;
@@ -952,8 +991,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
         uint4 *d4 = reinterpret_cast<uint4 *>(dst);
         for (int m = threadIdx.x; m < (total >> 3); m += blockDim.x) d4[m] = s4[m];
         for (int m = ((total >> 3) << 3) + threadIdx.x; m < total; m += blockDim.x) dst[m] = lst[m];
-        if (threadIdx.x == 0) s_tile = t_next;
+        if (threadIdx.x == 0) {
+            s_tile = t_next;
+            s_issued = issued_next;
+        }
         __syncthreads();
+        buf ^= 1;
+        have = pref;
     }
     if (err) atomicOr(&b.ctl->err, err);
     for (int o = 16; o > 0; o >>= 1) {
