@@ -188,57 +188,47 @@ __device__ __forceinline__ void block_sum3_ll(long long &a, long long &c, long l
     }
 }
 
-// Last block: per-replica totals from the per-tile partials, in tile order.
-// `fixed`: the partials are 64-bit integers, twice the energies in units of
-// 2^-22 (the FP32 path's exact, order-independent sums).
+// FP32 path: adds the block's energy sums (twice U, K and W in units of
+// 2^-22) to its replica's totals.  They are exact 64-bit integer sums, so the
+// order in which blocks add them does not change the result.  Called by every
+// thread of the block; the sums are zero afterwards.
+__device__ __forceinline__ void flush_energy(const Bufs &b, int r, long long &u, long long &k, long long &w,
+                                             long long (*sm)[3])
+{
+    block_sum3_ll(u, k, w, sm);
+    if (threadIdx.x == 0) {
+        unsigned long long *e = reinterpret_cast<unsigned long long *>(b.eacc + 4 * r);
+        if (u) atomicAdd(e + 0, (unsigned long long)u);
+        if (k) atomicAdd(e + 1, (unsigned long long)k);
+        if (w) atomicAdd(e + 2, (unsigned long long)w);
+    }
+    u = k = w = 0;
+    __syncthreads();   // sm is written again by the next flush
+}
+
+// Last block: per-replica totals.  `fixed` (the FP32 path): the per-replica
+// 64-bit integer sums that the blocks added, read and cleared for the next
+// launch.  Otherwise (FP64) the per-tile partials, summed in tile order.
 __device__ void reduce_partials(const Bufs &b, double *thermo, bool fixed)
 {
-    __shared__ double red[kBlock][3];
-    const long long *pl = reinterpret_cast<const long long *>(b.partial);
-    for (int r = 0; r < b.nrep; ++r) {
-        double a = 0, c = 0, d = 0;
-        if (fixed) {
-            long long la = 0, lc = 0, ld = 0;
-            // four tiles per thread and round, their loads all in flight at
-            // once (integer sums: the grouping does not change the result)
-            const int q1 = b.rep_tile[r + 1], bd = blockDim.x;
-            int q = b.rep_tile[r] + threadIdx.x;
-            for (; q + 3 * bd < q1; q += 4 * bd) {
-                long long ta[4], tc[4], td[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    ta[u] = pl[4 * (q + u * bd) + 0];
-                    tc[u] = pl[4 * (q + u * bd) + 1];
-                    td[u] = pl[4 * (q + u * bd) + 2];
-                }
-                la += (ta[0] + ta[1]) + (ta[2] + ta[3]);
-                lc += (tc[0] + tc[1]) + (tc[2] + tc[3]);
-                ld += (td[0] + td[1]) + (td[2] + td[3]);
-            }
-            for (; q < q1; q += bd) {
-                la += pl[4 * q + 0];
-                lc += pl[4 * q + 1];
-                ld += pl[4 * q + 2];
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                la += __shfl_down_sync(0xffffffffu, la, o);
-                lc += __shfl_down_sync(0xffffffffu, lc, o);
-                ld += __shfl_down_sync(0xffffffffu, ld, o);
-            }
-            __shared__ long long redl[kBlock / 32][3];
-            if ((threadIdx.x & 31) == 0) { redl[threadIdx.x >> 5][0] = la; redl[threadIdx.x >> 5][1] = lc; redl[threadIdx.x >> 5][2] = ld; }
-            __syncthreads();
-            if (threadIdx.x == 0 && thermo) {
-                la = lc = ld = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { la += redl[w][0]; lc += redl[w][1]; ld += redl[w][2]; }
+    if (fixed) {
+        for (int r = threadIdx.x; r < b.nrep; r += blockDim.x) {
+            unsigned long long *e = reinterpret_cast<unsigned long long *>(b.eacc + 4 * r);
+            const long long la = (long long)atomicExch(e + 0, 0ull);
+            const long long lc = (long long)atomicExch(e + 1, 0ull);
+            const long long ld = (long long)atomicExch(e + 2, 0ull);
+            if (thermo) {
                 constexpr double half_unit = 0.5 / 4194304.0;
                 thermo[3 * r + 0] = half_unit * ll_to_double(la);
                 thermo[3 * r + 1] = half_unit * ll_to_double(lc);
                 thermo[3 * r + 2] = half_unit * ll_to_double(ld);
             }
-            __syncthreads();
-            continue;
         }
+        return;
+    }
+    __shared__ double red[kBlock][3];
+    for (int r = 0; r < b.nrep; ++r) {
+        double a = 0, c = 0, d = 0;
         for (int q = b.rep_tile[r] + threadIdx.x; q < b.rep_tile[r + 1]; q += blockDim.x) {
             a += b.partial[4 * q + 0];
             c += b.partial[4 * q + 1];
@@ -379,7 +369,7 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, b
     fx_acc2(fs, dy, a.hy, a.ly);
     fx_acc2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        a.su.x += in ? s6 * (s6 - 1.0f) : 0.0f;
+        a.su.x += in ? __fmaf_rn(s6, s6, -s6) : 0.0f;
         a.sg.x += in ? g : 0.0f;
         a.nin += in ? 1 : 0;
     }
@@ -404,7 +394,7 @@ __device__ __forceinline__ void pair32x2(float2 dx, float2 dy, float2 dz, float2
     fx_acc2x2(fs, dy, a.hy, a.ly);
     fx_acc2x2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        const float2 e = __fmul2_rn(s6, __fadd2_rn(s6, make_float2(-1.0f, -1.0f)));
+        const float2 e = __ffma2_rn(s6, s6, make_float2(-s6.x, -s6.y));   // s6 (s6 - 1)
         a.su = __fadd2_rn(a.su, e);
         a.sg = __fadd2_rn(a.sg, g);
         a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
@@ -547,7 +537,7 @@ __device__ __forceinline__ void pair32x2_half(float2 dx, float2 dy, float2 dz, f
     if (in0) { red_sub(Fq + s0, x0); red_sub(Fq + S + s0, y0); red_sub(Fq + 2 * S + s0, z0); }
     if (in1) { red_sub(Fq + s1, x1); red_sub(Fq + S + s1, y1); red_sub(Fq + 2 * S + s1, z1); }
     if (ENERGY) {
-        const float2 e = __fmul2_rn(s6, __fadd2_rn(s6, make_float2(-1.0f, -1.0f)));
+        const float2 e = __ffma2_rn(s6, s6, make_float2(-s6.x, -s6.y));   // s6 (s6 - 1)
         a.su = __fadd2_rn(a.su, e);
         a.sg = __fadd2_rn(a.sg, g);
         a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
@@ -696,6 +686,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     int err = 0;
     int buf = 0;           // which tile buffer holds tile t
     bool have = false;     // whether it was prefetched
+    // FP32 path: energies as integers, twice the energy in units of 2^-22,
+    // summed over this block's tiles until the replica changes
+    long long uf = 0, wf = 0, kf = 0;
+    int rcur = -1;
     if (threadIdx.x == 0) {
         s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
         s_issued = 0;
@@ -716,6 +710,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         const Replica &R = b.rep[tl.rep];
         const int np = s_npb[buf];
         const int Pt = tl.s1 - tl.s0;
+        if (ENERGY && PREC == 1 && tl.rep != rcur) {   // block-uniform
+            if (rcur >= 0) flush_energy(b, rcur, uf, kf, wf, sml);
+            rcur = tl.rep;
+        }
         if (!HALF && pc[np].hoff > b.hcap) {          // the list build rejects such tiles first
             err |= kErrList;
             if (threadIdx.x == 0) { s_tile = t_next; s_issued = 0; }
@@ -766,8 +764,6 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             prefetch_tile_async(b, tn, tlb[buf ^ 1], pcb[buf ^ 1], s_npb[buf ^ 1], threadIdx.x & 31);
         const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
         double ui = 0.0, wi = 0.0, ki = 0.0;
-        // FP32 path: energies as integers, twice the energy in units of 2^-22
-        long long uf = 0, wf = 0, kf = 0;
         // Per particle: the pair sums (phase 1, which reads the staged halo
         // and list) and everything after them (phase 2: bonded terms, Langevin
         // force, integration, energies), which reads neither.
@@ -977,14 +973,14 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 if (ENERGY) {
                     double w2 = 0.0;
                     for (int k = 0; k < 3; ++k) { double w = b.v[cur][k * b.S + i]; w2 += w * w; }
-                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    if (PREC == 1) kf += fix_round(w2, b.mass * 4194304.0);
                     else ki += 0.5 * b.mass * w2;
                 }
             } else if (MODE == kModeStore) {
                 for (int k = 0; k < 3; ++k) b.F[k * b.S + i] = Fd[k] * fscale;
                 if (ENERGY) {
                     const double w2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    if (PREC == 1) kf += fix_round(w2, b.mass * 4194304.0);
                     else ki += 0.5 * b.mass * w2;
                 }
             } else if (MODE == kModeFinal) {
@@ -996,7 +992,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 }
                 if (ENERGY) {
                     const double w2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    if (PREC == 1) kf += fix_round(w2, b.mass * 4194304.0);
                     else ki += 0.5 * b.mass * w2;
                 }
             } else {  // kModeFused: end of step n, then the first half kick and drift of step n + 1
@@ -1005,7 +1001,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 for (int k = 0; k < 3; ++k) v[k] += c * Fd[k];
                 if (ENERGY) {
                     const double w2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                    if (PREC == 1) kf += fix_round(b.mass * w2, 4194304.0);
+                    if (PREC == 1) kf += fix_round(w2, b.mass * 4194304.0);
                     else ki += 0.5 * b.mass * w2;
                 }
                 for (int k = 0; k < 3; ++k) {
@@ -1047,20 +1043,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 phase2(i, ps);
             }
         }
-        if (ENERGY && PREC == 1) {
-            block_sum3_ll(uf, kf, wf, sml);
-            if (threadIdx.x == 0) {
-                long long *pl = reinterpret_cast<long long *>(b.partial);
-                if (HALF) {   // k_pairs_half wrote the tile's pair energy and virial
-                    pl[4 * t + 0] += uf;
-                    pl[4 * t + 2] += wf;
-                } else {
-                    pl[4 * t + 0] = uf;
-                    pl[4 * t + 2] = wf;
-                }
-                pl[4 * t + 1] = kf;
-            }
-        } else if (ENERGY) {
+        if (ENERGY && PREC != 1) {
             double a = ui, c = ki, d = wi;
             block_sum3(a, c, d, sm3);
             if (threadIdx.x == 0) {
@@ -1078,6 +1061,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         buf ^= 1;
         have = pref;
     }
+    if (ENERGY && PREC == 1 && rcur >= 0) flush_energy(b, rcur, uf, kf, wf, sml);
     if (err) atomicOr(&b.ctl->err, err);
     constexpr bool kDrift = (MODE == kModeFused);
     if (kDrift) ratio = block_max(ratio, smr);
@@ -1106,6 +1090,8 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
     uint4 *hpos = reinterpret_cast<uint4 *>(smem_raw);
     unsigned short *lst = reinterpret_cast<unsigned short *>(smem_raw + (size_t)b.hcap * sizeof(uint4));
     int err = 0;
+    long long uf = 0, kf = 0, wf = 0;   // summed over this block's tiles until the replica changes
+    int rcur = -1;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
     __syncthreads();
     for (;;) {
@@ -1119,6 +1105,10 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
         const Replica &R = b.rep[tl.rep];
         const int np = s_np;
         const int Pt = tl.s1 - tl.s0;
+        if (ENERGY && tl.rep != rcur) {   // block-uniform
+            if (rcur >= 0) flush_energy(b, rcur, uf, kf, wf, sml);
+            rcur = tl.rep;
+        }
         if (pc[np].hoff > b.hcap) {
             err |= kErrList;
             if (threadIdx.x == 0) s_tile = t_next;
@@ -1145,7 +1135,6 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
         // the fourth word of every staged position becomes its slot
         stage_halo<uint4>(pc, np, [&](int h, int j) { hpos[h].w = (unsigned)j; });
         __syncthreads();
-        long long uf = 0, kf = 0, wf = 0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
             const uint4 pi = hpos[s_self + (int)(i - tl.s0)];
             const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
@@ -1169,17 +1158,10 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
                 wf += fx_round(2.0f * (R.eps24_f * (a.sg.x + a.sg.y)));
             }
         }
-        if (ENERGY) {
-            block_sum3_ll(uf, kf, wf, sml);
-            if (threadIdx.x == 0) {
-                long long *pl = reinterpret_cast<long long *>(b.partial);
-                pl[4 * t + 0] = uf;
-                pl[4 * t + 2] = wf;
-            }
-        }
         if (threadIdx.x == 0) s_tile = t_next;
         __syncthreads();   // the halo and the tile record are reused by the next tile
     }
+    if (ENERGY && rcur >= 0) flush_energy(b, rcur, uf, kf, wf, sml);
     if (err) atomicOr(&b.ctl->err, err);
     finish(b, false, false, true, 0.0f, true);
 }

@@ -529,6 +529,7 @@ md_status md_create(const md_params *p, md_handle **out)
     ok &= (b.bucket = dalloc<int>(h, h->S)) != nullptr;
     ok &= (b.nn = dalloc<int>(h, h->S)) != nullptr;
     ok &= (b.partial = dalloc<double>(h, 4 * (size_t)h->C)) != nullptr;
+    ok &= (b.eacc = dalloc<long long>(h, 4 * (size_t)nrep)) != nullptr;
     ok &= (b.tiles = dalloc<mdk::Tile>(h, h->C)) != nullptr;
     ok &= (b.pieces = dalloc<mdk::Piece>(h, (size_t)h->C * (mdk::kMaxPieces + 1))) != nullptr;
     ok &= (b.tile_np = dalloc<int>(h, h->C)) != nullptr;
@@ -562,6 +563,7 @@ md_status md_create(const md_params *p, md_handle **out)
     ok &= cudaMemcpy(dblk, blk.data(), sizeof(int) * h->nblk, cudaMemcpyHostToDevice) == cudaSuccess;
     ok &= cudaMemset(b.cell_count, 0, sizeof(int) * h->C) == cudaSuccess;
     ok &= cudaMemset(b.ctl, 0, sizeof(Ctl)) == cudaSuccess;
+    ok &= cudaMemset(b.eacc, 0, sizeof(long long) * 4 * (size_t)nrep) == cudaSuccess;
     b.rep = drep;
     b.blk_rep = dblk;
 
@@ -648,8 +650,10 @@ md_status md_set_state(md_handle *h, const double *x, const double *v, void *str
         !cuda_ok(h, cudaMemcpyAsync(vs, v, bytes, cudaMemcpyDefault, st), "copy velocities") ||
         !cuda_ok(h, cudaMemsetAsync(h->b.cell_count, 0, sizeof(int) * h->C, st), "clear cells"))
         return MD_ERR_CUDA;
-    // half list: a step cut short by a latched error can leave sums behind
+    // a launch cut short by a latched error can leave sums behind
     if (h->b.Fq && !cuda_ok(h, cudaMemsetAsync(h->b.Fq, 0, sizeof(long long) * 3 * h->S, st), "clear force sums"))
+        return MD_ERR_CUDA;
+    if (!cuda_ok(h, cudaMemsetAsync(h->b.eacc, 0, sizeof(long long) * 4 * (size_t)h->b.nrep, st), "clear energy sums"))
         return MD_ERR_CUDA;
     mdk::launch_set_state(h->b, xs, vs, st);
     if (!cuda_ok(h, cudaGetLastError(), "set_state launch")) return MD_ERR_CUDA;
@@ -703,6 +707,8 @@ md_status md_build_neighbors(md_handle *h, void *stream)
         if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
             return MD_ERR_CUDA;
         if (h->b.Fq && !cuda_ok(h, cudaMemset(h->b.Fq, 0, sizeof(long long) * 3 * h->S), "clear force sums"))
+            return MD_ERR_CUDA;
+        if (!cuda_ok(h, cudaMemset(h->b.eacc, 0, sizeof(long long) * 4 * (size_t)h->b.nrep), "clear energy sums"))
             return MD_ERR_CUDA;
         // the overflowing build still sorted the state; build again with the larger capacities
         mdk::launch_set_rebuild(h->b, st);

@@ -176,6 +176,8 @@ struct Bufs {
     uint4 *pos[2];
     double *F;               // stored total force of the current state, 3 * S, slot order
     long long *Fq;           // half list: 64-bit fixed-point force sums (3 * S, slot order), zero between steps
+    long long *eacc;         // FP32 path: per-replica energy sums (4 * nrep: U, K, W, unused; twice the
+                             // energies in units of 2^-22), zero between launches
     int half_list;           // 1: each pair once (Newton's third law), reactions by 64-bit atomics
     uint4 *xref;
     int *slot_of_id;         // N
