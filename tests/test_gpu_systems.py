@@ -68,6 +68,54 @@ def test_replicas_forces_energies_pairs(md, precision):
     assert np.all(pairs[:, 1] < np.repeat(off[1:], np.diff(off))[pairs[:, 0]])   # no pair across replicas
 
 
+def test_many_replicas_energy_sums(md):
+    """160 replicas of 500 particles (about 1,400 tiles, more than the
+    persistent blocks, so most blocks take tiles of several replicas in turn
+    and add their energy sums per replica as the replica changes): forces and
+    (U, K, W) of every replica match the oracle run on it alone, in FP32 with
+    fixed-point sums; 10 steps with (U, K, W) recorded every step keep every
+    record finite and the last one equal to a force evaluation of the final
+    state in U and W."""
+    R = 160
+    rng = np.random.default_rng(77)
+    sizes, boxes, eps, sig, xs, vs = [], [], [], [], [], []
+    for r in range(R):
+        s = rng.uniform(0.95, 1.05)
+        x, v, box = inputs.perturbed_lattice(5, seed=300 + r, amp=0.1)
+        xs.append(x * s); vs.append(v)
+        sizes.append(len(x)); boxes.append(box * s); eps.append(rng.uniform(0.9, 1.1)); sig.append(s)
+    X, V = np.concatenate(xs), np.concatenate(vs)
+    N = len(X)
+    h = md.md_create(sizes, np.array(boxes), eps=np.array(eps), sigma=np.array(sig), precision=md.MD_FP32_FIXED)
+    md.md_set_state(h, dev(X), dev(V))
+    md.md_build_neighbors(h)
+    f = torch.zeros(3, N, dtype=torch.float64, device="cuda")
+    euw = torch.zeros(R, 3, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, euw)
+    md.md_sync(h)
+    F, E = host(f), euw.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for r in range(R):
+        s = oracle.System(sizes[r], boxes[r], eps=eps[r], sigma=sig[r], rc=2.5 * sig[r])
+        Fr, er = oracle.forces(s, xs[r], vs[r])
+        assert force_rel_err(F[off[r]:off[r + 1]], Fr) <= TOL[1]
+        np.testing.assert_allclose(E[r], er, rtol=TOL[1], atol=TOL[1] * sizes[r])
+    # a second evaluation gives the same sums (the accumulators were cleared)
+    euw2 = torch.zeros(R, 3, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, euw2)
+    md.md_sync(h)
+    np.testing.assert_array_equal(euw2.cpu().numpy(), E)
+    th = np.zeros((10, R, 3))
+    md.md_step(h, 10, 1, th)
+    assert np.all(np.isfinite(th))
+    euw3 = torch.zeros(R, 3, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, euw3)
+    md.md_sync(h)
+    e3 = euw3.cpu().numpy()
+    np.testing.assert_array_equal(th[-1][:, 0], e3[:, 0])
+    np.testing.assert_array_equal(th[-1][:, 2], e3[:, 2])
+
+
 def test_replicas_trajectory_fp64(md):
     """Two replicas stepped together follow the oracle run on each alone."""
     a = inputs.lj_fluid(5, T=0.72, seed=51)
