@@ -239,6 +239,42 @@ def test_automatic_capacity_grows(md):
     np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lists_longer_than_the_shared_stage(md, precision):
+    """A compressed fcc crystal (rho = 1.2, N = 4000) with a skin of 0.8: about
+    180 neighbours within r_cut + r_skin, more rows than the list build stages
+    in shared memory for a tile of about 125 particles (12288 entries), so the
+    rows beyond the stage are written straight to global memory, and the force
+    kernel reads those tiles' lists from global memory instead of staging
+    them.  The pair set equals brute force, forces and energies follow the
+    oracle, and 10 steps split 4 + 6 equal 10 in one call bit for bit."""
+    skin = 0.8
+    x, v, box = inputs.perturbed_lattice(10, rho=1.2, seed=21, amp=0.05)
+    n = len(x)
+    h = make(md, x, v, box, precision, skin=skin)
+    assert md.md_get_stats(h)["max_list_len"] > 128
+    got = md.export_pairs_sorted(h)
+    want, _ = oracle.pairs(oracle.System(n, box, rc=RC), x, RC + skin)
+    np.testing.assert_array_equal(got, want)
+    F, euw = gpu_forces(md, h, n)
+    F_ref, e_ref = oracle.forces(oracle.System(n, box, rc=RC), x, v)
+    tol = TOL[precision]
+    assert force_rel_err(F, F_ref) <= tol
+    for k in range(3):
+        assert euw[0, k] == pytest.approx(e_ref[k], rel=tol, abs=tol * n)
+    states = []
+    for parts in ((10,), (4, 6)):
+        hs = make(md, x, v, box, precision, skin=skin)
+        for k in parts:
+            md.md_step(hs, k)
+        xo = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+        vo = torch.zeros_like(xo)
+        md.md_get_state(hs, xo, vo)
+        states.append((xo.cpu().numpy(), vo.cpu().numpy()))
+    np.testing.assert_array_equal(states[0][0], states[1][0])
+    np.testing.assert_array_equal(states[0][1], states[1][1])
+
+
 def test_thermo_every_step_graph_equals_stream_launches(md):
     """md_step with (U, K, W) every step runs as one graph launch; with the
     section timers on the same kernels are launched one by one.  Both give
