@@ -757,9 +757,10 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             break;
         }
         // the last warp copies the next tile's record and pieces into the other
-        // buffer while the tile is computed
+        // buffer while the tile is computed (not in the half-list pass, which
+        // stages nothing and has little work per tile to hide the copy behind)
         const int tn = s_next;
-        const bool pref = tn < b.ctl->ntiles;
+        const bool pref = !HALF && tn < b.ctl->ntiles;
         if (pref && threadIdx.x >= blockDim.x - 32)
             prefetch_tile_async(b, tn, tlb[buf ^ 1], pcb[buf ^ 1], s_npb[buf ^ 1], threadIdx.x & 31);
         const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
