@@ -326,7 +326,10 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, flo
             if (b.g_while) {                    // inside the graph's step loop
                 const long long left = b.ctl->steps_left - 1;
                 b.ctl->steps_left = left;
-                cudaGraphSetConditional(b.g_while, left > 0 ? 1u : 0u);
+                // every block has added its error bits before counting itself
+                // done, so an error latched by this launch ends the loop now
+                const int e = *(volatile int *)&b.ctl->err;
+                cudaGraphSetConditional(b.g_while, (left > 0 && e == 0) ? 1u : 0u);
             }
         }
         if (tiled) b.ctl->tile_next = 0u;
@@ -664,7 +667,12 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
     __shared__ float smr[kBlock / 32];
     __shared__ __align__(8) unsigned long long s_mbar;   // completion of a tile's bulk copies
     __shared__ __align__(8) unsigned long long s_p1bar;  // every thread past its pair sums
-    if (block_uniform(b.ctl->err != 0)) return;
+    if (block_uniform(b.ctl->err != 0)) {
+        // inside a graph-launched step loop nothing else would clear the
+        // loop's condition: a latched error ends the loop here
+        if (b.g_while && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(b.g_while, 0u);
+        return;
+    }
     // FP32 full-list tiles are staged by bulk (TMA) copies: thread 0 arms the
     // barrier and copies the halo pieces and the list block, all threads wait
     constexpr bool kBulk = (PREC == 1 && !HALF);
@@ -1264,5 +1272,19 @@ void launch_force(const Bufs &b, int precision, int mode, bool energy, cudaStrea
 }
 
 void launch_kick_drift(const Bufs &b, cudaStream_t st) { k_kick_drift<<<b.nblk, kBlock, 0, st>>>(b); }
+
+// The bounded wait of the tile kernels on a barrier that no arrival and no
+// copy will complete: every thread gives up after `polls` polls and the
+// block latches the timeout, as a block whose bulk copies never arrived does.
+__global__ void __launch_bounds__(kBlock) k_wait_selftest(Bufs b, int polls)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool late = !mbar_wait(&bar, 0u, polls);
+    if (__syncthreads_or(late) && threadIdx.x == 0) atomicOr(&b.ctl->err, kErrTimeout);
+}
+
+void launch_wait_selftest(const Bufs &b, int polls, cudaStream_t st) { k_wait_selftest<<<1, kBlock, 0, st>>>(b, polls); }
 
 }  // namespace mdk
