@@ -97,7 +97,8 @@ def lib():
         L.orc_loss_grad.restype = None
         L.orc_loss_grad.argtypes = [sp, dp, dp, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp]
         L.orc_vv_adjoint.restype = C.c_int
-        L.orc_vv_adjoint.argtypes = [sp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp, dp]
+        L.orc_vv_adjoint.argtypes = [sp, dp, dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, dp, dp, dp, dp,
+                                     dp, dp]
         L.orc_set_rc_fixed.restype = None
         L.orc_set_rc_fixed.argtypes = [C.c_int]
         L.orc_num_threads.restype = C.c_int
@@ -330,19 +331,24 @@ def hvp(sysm, x, w):
     return hv, pe.value, ps.value
 
 
-def vv_adjoint(sysm, x, v, nsteps, cU, cK, cW, rc_fixed=False):
-    """Adjoint of nsteps NVE velocity-Verlet steps for L = cU U + cK K + cW W at
-    the end.  Returns (euw_T, dL/deps, dL/dsigma, lx0, lv0).  By default r_cut
-    moves with sigma (sysm.rc is rc_over_sigma * sigma); rc_fixed=True holds it."""
+def vv_adjoint(sysm, x, v, nsteps, cU, cK, cW, rc_fixed=False, gx=None, gv=None):
+    """Adjoint of nsteps NVE velocity-Verlet steps for L = cU U + cK K + cW W +
+    gx . x_T + gv . v_T at the end (gx, gv: (N, 3) gradients of the loss in
+    the final positions and velocities, or None).  Returns (euw_T, dL/deps,
+    dL/dsigma, lx0, lv0).  By default r_cut moves with sigma (sysm.rc is
+    rc_over_sigma * sigma); rc_fixed=True holds it."""
     lib().orc_set_rc_fixed(1 if rc_fixed else 0)
     x = _f64(x, (sysm.n, 3))
     v = _f64(v, (sysm.n, 3))
+    gxa = None if gx is None else _f64(gx, (sysm.n, 3))
+    gva = None if gv is None else _f64(gv, (sysm.n, 3))
     euw = np.zeros(3)
     ge, gs = C.c_double(), C.c_double()
     lx = np.zeros((sysm.n, 3))
     lv = np.zeros((sysm.n, 3))
     s = sysm.c()
     rc = lib().orc_vv_adjoint(C.byref(s), _dp(x), _dp(v), int(nsteps), float(cU), float(cK), float(cW),
+                              None if gxa is None else _dp(gxa), None if gva is None else _dp(gva),
                               _dp(euw), C.byref(ge), C.byref(gs), _dp(lx), _dp(lv))
     if rc != 0:
         raise RuntimeError(f"oracle vv_adjoint failed: {rc}")

@@ -670,11 +670,14 @@ void orc_loss_grad(const orc_system *s, const double *x, const double *v, double
 
 /* Reverse pass through nsteps NVE velocity-Verlet steps from (x0, v0):
  * runs the forward (keeping every position), then the adjoint of each step
- * (half kick, drift, half kick, in reverse).  Outputs the final (U, K, W),
- * dL/deps, dL/dsigma, and the adjoints lx0, lv0 of the initial state. */
+ * (half kick, drift, half kick, in reverse).  The loss is
+ * L = cU U + cK K + cW W + gx . x_T + gv . v_T at the final state; gx and gv
+ * ((N, 3) each, either may be NULL) are the loss's own gradients in the final
+ * positions and velocities.  Outputs the final (U, K, W), dL/deps, dL/dsigma,
+ * and the adjoints lx0, lv0 of the initial state. */
 int orc_vv_adjoint(const orc_system *s, const double *x0, const double *v0, int64_t nsteps,
-                   double cU, double cK, double cW, double *euw, double *g_eps, double *g_sig,
-                   double *lx0, double *lv0)
+                   double cU, double cK, double cW, const double *gx, const double *gv, double *euw,
+                   double *g_eps, double *g_sig, double *lx0, double *lv0)
 {
     int64_t n = s->n;
     size_t sz = (size_t)(3 * n);
@@ -702,6 +705,10 @@ int orc_vv_adjoint(const orc_system *s, const double *x0, const double *v0, int6
     double ge, gs;
     double *lx = lx0, *lv = lv0;
     orc_loss_grad(s, xT, v, cU, cK, cW, lx, lv, &ge, &gs);
+    for (size_t q = 0; q < sz; ++q) {
+        if (gx) lx[q] += gx[q];
+        if (gv) lv[q] += gv[q];
+    }
     for (int64_t t = nsteps; t >= 0 && nsteps > 0; --t) {
         /* kick(s) at x_t: the first half kick of step t and the second of step t-1 */
         double c = (t == nsteps || t == 0) ? h : 2.0 * h;

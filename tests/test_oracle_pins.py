@@ -430,6 +430,43 @@ def test_adjoint_initial_state_gradient():
         assert np.sum(lv * dv) == pytest.approx(fv, rel=1e-5)
 
 
+def test_adjoint_of_a_loss_on_the_final_state():
+    """A loss on the end point itself, L = gx . x_T + gv . v_T: with gx and gv
+    as the terminal adjoints the reverse pass gives dL/deps, dL/dsigma and
+    dL/d(x0, v0) equal to central differences of the forward (r_cut held
+    fixed for sigma; x_T compared by minimum image, as positions wrap)."""
+    x, v, box = _liquid(ncell=3, seed=7, amp=0.1)
+    n = len(x)
+    T = 4
+    rng = np.random.default_rng(12)
+    gx, gv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+
+    def end(eps=1.0, sig=1.0, xx=x, vv=v):
+        s = oracle.System(n, box, eps=eps, sigma=sig, rc=2.5, dt=0.005)
+        x1, v1, _ = oracle.vv_run(s, xx, vv, T)
+        return x1, v1
+
+    def dL(a, b):
+        d = a[0] - b[0]
+        d -= box * np.round(d / box)
+        return float(np.sum(gx * d) + np.sum(gv * (a[1] - b[1])))
+
+    s = oracle.System(n, box, rc=2.5, dt=0.005)
+    euw, ge, gs, lx, lv = oracle.vv_adjoint(s, x, v, T, 0.0, 0.0, 0.0, rc_fixed=True, gx=gx, gv=gv)
+    h = 1e-6
+    assert ge == pytest.approx(dL(end(eps=1 + h), end(eps=1 - h)) / (2 * h), rel=1e-6)
+    assert gs == pytest.approx(dL(end(sig=1 + h), end(sig=1 - h)) / (2 * h), rel=1e-6)
+    dx, dv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    assert np.sum(lx * dx) == pytest.approx(dL(end(xx=x + h * dx), end(xx=x - h * dx)) / (2 * h), rel=1e-6)
+    assert np.sum(lv * dv) == pytest.approx(dL(end(vv=v + h * dv), end(vv=v - h * dv)) / (2 * h), rel=1e-6)
+    # the terms add: the energy loss and the end-point loss together give the sum
+    c = (1.0 / n, 0.3, 0.2)
+    _, ge_c, gs_c, _, _ = oracle.vv_adjoint(s, x, v, T, *c, rc_fixed=True)
+    _, ge_b, gs_b, _, _ = oracle.vv_adjoint(s, x, v, T, *c, rc_fixed=True, gx=gx, gv=gv)
+    assert ge_b == pytest.approx(ge_c + ge, rel=1e-12)
+    assert gs_b == pytest.approx(gs_c + gs, rel=1e-12)
+
+
 # ---------------------------------------------------------------- soft push-off
 def test_soft_pushoff_closed_forms_and_derivative():
     """Cosine push-off A (1 + cos(pi r / rc)): V(0) = 2A, V(rc/2) = A, V(rc) = 0;
