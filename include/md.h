@@ -114,6 +114,7 @@ typedef struct {
     int32_t max_halo;           /* largest tile halo (particles) at the last build */
     int32_t halo_capacity;      /* shared-memory halo capacity (particles)    */
     int32_t tile_size;          /* particles per tile the tiler aims at        */
+    int64_t recoveries;         /* md_step overflows recovered (md_set_recovery) */
 } md_stats;
 
 /* Create a handle for the replicas described by p (Sec. 2.1: cells of edge
@@ -123,18 +124,45 @@ typedef struct {
  * NULL on failure. */
 md_status md_create(const md_params *p, md_handle **out);
 
-/* Free everything the handle owns.  Synchronises the device first. */
+/* Free everything the handle owns.  Synchronises the device first.  No
+ * passage of the paper: resource lifetime of this library. */
 void md_destroy(md_handle *h);
 
 /* Load positions x and velocities v, each (3, N) component-major FP64, into the
- * handle; positions are wrapped into [0, L).  Resets the step counter, marks
- * the neighbour list stale and the stored force invalid.  Asynchronous. */
+ * handle; positions are wrapped into [0, L).  These are the particle state
+ * (r_i, v_i) that velocity Verlet advances (Fig. 1; Eq. 1).  Resets the step
+ * counter, marks the neighbour list stale and the stored force invalid.  A
+ * non-finite value latches MD_ERR_NONFINITE (reported by the next
+ * synchronising call).  Asynchronous.  To resume a saved run exactly, use
+ * md_set_checkpoint instead. */
 md_status md_set_state(md_handle *h, const double *x, const double *v, void *stream);
 
 /* Copy the current positions and velocities out, (3, N) FP64 each, in the
- * caller's particle order.  Either pointer may be NULL.  Synchronises `stream`
- * and returns any latched device error. */
+ * caller's particle order: the state (r_i, v_i) of Fig. 1 after the last
+ * completed step.  Either pointer may be NULL.  Synchronises `stream` and
+ * returns any latched device error. */
 md_status md_get_state(md_handle *h, double *x, double *v, void *stream);
+
+/* Save everything the next step depends on, so that a run can be stopped and
+ * resumed exactly: positions x and velocities v ((3, N) FP64 each, as
+ * md_get_state), the stored total force f ((3, N) FP64: the force of Fig. 1's
+ * second half kick, which the next step's first half kick reuses, including
+ * the Langevin term of Sec. 4's thermostatted runs), and the step counter
+ * *step (host), which keys the Langevin noise.  Caller order; host or device
+ * pointers, none NULL.  When the handle holds no stored force (no md_step
+ * since the last md_set_state, md_build_neighbors or md_compute_forces) it is
+ * evaluated now, as the next md_step would.  Synchronises `stream` and returns
+ * any latched device error. */
+md_status md_get_checkpoint(md_handle *h, double *x, double *v, double *f, int64_t *step, void *stream);
+
+/* Restore a state saved by md_get_checkpoint: md_set_state(x, v), then the step
+ * counter and the stored force, with the cells and the Verlet list built at x.
+ * The following md_step continues the saved run: bit for bit in
+ * MD_FP32_FIXED (its sums do not depend on when the list was built), to
+ * rounding in MD_FP64, with the same Langevin noise in both.  MD_ERR_ARG for a
+ * NULL pointer or step < 0.  Synchronises `stream`. */
+md_status md_set_checkpoint(md_handle *h, const double *x, const double *v, const double *f, int64_t step,
+                            void *stream);
 
 /* Bin particles into cells with a counting sort and rebuild the Verlet list of
  * all pairs with |d| < r_cut + r_skin (Sec. 2.1.2), now, whatever the
@@ -159,6 +187,31 @@ md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *
  * FP64 each.  Asynchronous; device errors are latched. */
 md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream);
 
+/* Overflow recovery for md_step.  The Verlet list (Sec. 2.1.2) and each
+ * tile's staged halo have fixed capacities; a rebuild that md_step runs on
+ * the device can outgrow them when the system densifies.  With enable = 1,
+ * md_step synchronises its stream at the start and the end of every call and,
+ * if a rebuild inside the call overflowed, grows the capacity that overflowed
+ * (also a list_capacity given at md_create), rebuilds the list from the state
+ * at which that rebuild ran, and runs the rest of the call's steps; the result
+ * equals an uninterrupted run with the larger capacity (bit for bit in
+ * MD_FP32_FIXED), energy records included.  md_get_stats counts the
+ * recoveries.  With enable = 0 (the default) md_step stays asynchronous and an
+ * overflow is latched as MD_ERR_LIST_OVERFLOW: the call's remaining kernels
+ * return at once and the error is reported by the next synchronising call. */
+md_status md_set_recovery(md_handle *h, int32_t enable);
+
+/* Self-test of the bounded device waits.  Every wait of the library's kernels
+ * (the completion of a tile's bulk copies) gives up after a bounded number of
+ * polls and latches MD_ERR_TIMEOUT instead of hanging the GPU.  This call
+ * launches one block that waits, with the same code, on a barrier that
+ * nothing completes, polling at most `polls` times (1..65536; each poll may
+ * suspend the thread for a short, hardware-defined time), so that the error
+ * path can be exercised: the next synchronising call returns MD_ERR_TIMEOUT,
+ * and md_set_state (or md_set_checkpoint) clears it.  The paper has no
+ * counterpart.  MD_ERR_ARG for polls outside 1..65536.  Asynchronous. */
+md_status md_check_wait_timeout(md_handle *h, int32_t polls, void *stream);
+
 /* Differentiable run (reverse-mode differentiation of the velocity-Verlet map
  * of Fig. 1; the paper itself has no gradients).  Advance nsteps NVE steps from
  * the current state, keeping (x, v) every ckpt_every steps in device memory the
@@ -169,15 +222,23 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
  * Synchronises `stream`. */
 md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *euw_out, void *stream);
 
-/* Reverse pass of the last md_forward for a loss L(U, K, W) of its final state.
- * dL_deuw: (dL/dU, dL/dK, dL/dW) per replica, 3 * n_replicas FP64, host or
- * device.  Writes dL/deps and dL/dsigma per replica (n_replicas FP64 each, host
- * or device): the derivative of the smooth flow, with r_cut = rc_over_sigma *
+/* Reverse pass of the last md_forward (the adjoint of the velocity-Verlet map
+ * of Fig. 1) for a loss L of its final state:
+ *   dL_dx, dL_dv: the loss's gradients in the final positions and velocities,
+ *                 (3, N) FP64 each in the caller's order, host or device, or
+ *                 NULL (zero): a loss on the trajectory's end point itself,
+ *                 such as a target structure or a displacement;
+ *   dL_deuw:      (dL/dU, dL/dK, dL/dW) per replica, 3 * n_replicas FP64,
+ *                 host or device, or NULL (zero): a loss on the final energies
+ *                 and virial.
+ * Writes dL/deps and dL/dsigma per replica (n_replicas FP64 each, host or
+ * device): the derivative of the smooth flow, with r_cut = rc_over_sigma *
  * sigma moving with sigma (pairs crossing r_cut contribute jump terms that are
  * not included).  Recomputes each segment from its checkpoint; Hessian-vector
  * products and all adjoint sums in FP64.  Leaves the handle at the final state
  * of the recorded run (step counter and stats reset).  Synchronises `stream`. */
-md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, double *dL_dsigma, void *stream);
+md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, const double *dL_deuw,
+                      double *dL_deps, double *dL_dsigma, void *stream);
 
 /* Export the current Verlet pair set as pairs (i, j), i < j, in the caller's
  * particle numbering, in no particular order.  Writes at most `capacity` pairs
@@ -225,7 +286,9 @@ md_status md_set_half_list(md_handle *h, int32_t enable, void *stream);
 /* Wait for all work on `stream` and return any latched device error. */
 md_status md_sync(md_handle *h, void *stream);
 
-/* Counters and latched errors; synchronises the device. */
+/* Counters and latched errors; synchronises the device.  The counters are
+ * those the paper reports for its runs (Sec. 4: steps, neighbour-list
+ * rebuilds, neighbours per particle); the error word is this library's. */
 md_status md_get_stats(md_handle *h, md_stats *out);
 
 /* Section timers.  Sec. 4 of the paper splits the elapsed time of the
@@ -245,30 +308,42 @@ md_status md_set_timing(md_handle *h, int32_t enable);
  * Synchronises the device. */
 md_status md_get_timing(md_handle *h, double *ms, int64_t *counts);
 
-/* Force evaluation that allocates nothing, for callers that cannot allocate
- * device memory (code running while a stream is captured into a CUDA graph,
- * where cudaMalloc is not allowed, or a host framework that owns all device
- * memory).  The paper has no counterpart: it is a convenience of this library.
+/* Force evaluation that allocates nothing, for callers that cannot call
+ * cudaMalloc: a host framework that owns every byte of device memory through
+ * its own pool and forbids other allocators, or a process whose device memory
+ * is already committed to a fixed budget.  The paper has no counterpart: it is
+ * a convenience of this library.
  *
- * Computes the same conservative pair forces as md_compute_forces (shifted LJ
+ * Computes only the non-bonded pair term of md_compute_forces (shifted LJ
  * when shift != 0, r < rc strict, minimum image in the orthorhombic box, FP32
  * pairs with 64-bit fixed-point sums or FP64), summed directly over all pairs
  * without cells or Verlet lists (O(n^2)), for ONE system of n particles.
+ * FENE bonds and angle triples are not evaluated: for a system with bonded
+ * terms the result differs from md_compute_forces.
  *   x      device, (3, n) FP64 positions      v     device, (3, n) or NULL (K = 0)
  *   box    host, 3 edges, each >= 2 rc        f_out device, (3, n) FP64 forces
  *   euw_out device, 3 FP64 (U, K, W) or NULL  err_msg/err_len optional host text buffer
+ * Range: in MD_FP32_FIXED a pair closer than the fixed-point range allows
+ * (|f| of one component near 2^21, r of about 0.44 sigma for LJ with eps = 1)
+ * or two coincident particles make the force rows of both particles and the
+ * U and W of euw_out NaN (K, from the velocities, is unaffected); the call
+ * itself still returns MD_OK (it does not synchronise).
+ * In MD_FP64 coincident particles give non-finite values.
  * Limits: 1 <= n <= 524288 (the fixed scratch), else MD_ERR_ARG with a message.
  * Scratch: a fixed 64 KB device array in the library, held by every GPU that
  * loads it until the process exits; every call shares it, so calls that
  * overlap on the GPU race.  Nothing is allocated or freed.  The first call on
- * a device looks up the scratch address with that device current; make that
+ * a device looks up the scratch address with that device current and keeps
+ * it for the life of the process (a cudaDeviceReset, which ends the primary
+ * context, leaves a stale address: do not call this after one); make that
  * first call before any stream capture.  Asynchronous on `stream`. */
 md_status md_compute_forces_noalloc(const double *x, const double *v, int64_t n, const double *box,
                                     double eps, double sigma, double rc, int32_t shift, int32_t precision,
                                     double mass, double *f_out, double *euw_out, char *err_msg,
                                     int32_t err_len, void *stream);
 
-/* Text of the last error on this handle ("" if none).  Valid until the next call. */
+/* Text of the last error on this handle ("" if none).  Valid until the next
+ * call.  No passage of the paper: error reporting of this library. */
 const char *md_last_error(const md_handle *h);
 
 #ifdef __cplusplus

@@ -356,6 +356,16 @@ __global__ void k_adj_update(long long n3, double *lx, double *lv, const double 
     }
 }
 
+// Terminal adjoints of a loss on the final state itself: lx += dL/dx_T,
+// lv += dL/dv_T (caller order, 3 N values each; either input may be null).
+__global__ void k_adj_add(long long n3, double *lx, double *lv, const double *gx, const double *gv)
+{
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n3; q += (long long)gridDim.x * blockDim.x) {
+        if (gx) lx[q] += gx[q];
+        if (gv) lv[q] += gv[q];
+    }
+}
+
 // Explicit parameter terms of the loss from the per-replica sums (U, W, Ws):
 // g_eps += (cU U + cW W) / eps, g_sigma += cU W / sigma + cW Ws (r_cut moves
 // with sigma, so dU/dsigma = W / sigma); g holds (g_eps, g_sigma, -, -) per replica.
@@ -418,6 +428,11 @@ void launch_adj_finish_loss(const Bufs &b, const double *sums, const double *coe
 void launch_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt, cudaStream_t st)
 {
     k_adj_update<<<(unsigned)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, st>>>(n3, lx, lv, hv, c, dt);
+}
+
+void launch_adj_add(long long n3, double *lx, double *lv, const double *gx, const double *gv, cudaStream_t st)
+{
+    k_adj_add<<<(unsigned)std::min<long long>((n3 + 255) / 256, 4096), 256, 0, st>>>(n3, lx, lv, gx, gv);
 }
 
 }  // namespace mdk

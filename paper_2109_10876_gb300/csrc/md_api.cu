@@ -57,6 +57,10 @@ struct md_handle {
     cudaGraph_t graph_e = nullptr;
     long long gen = 0, gexec_gen = -1, gexec_e_gen = -1;   // gen: bumped whenever the kernels' buffers change
     bool use_graph = true;
+    // md_set_recovery: md_step grows the list / halo capacity and finishes the
+    // call when a rebuild inside it overflowed
+    bool recover = false;
+    long long recoveries = 0;
 };
 
 namespace {
@@ -304,6 +308,36 @@ bool build_step_graph(md_handle *h, bool energy)
     if (cudaGraphInstantiate(&gexec, G, 0) != cudaSuccess) { gexec = nullptr; return false; }
     ggen = h->gen;
     return true;
+}
+
+// After a list or halo overflow (c.err == kErrList): grow the list capacity
+// and / or the halo capacity to fit what the failed build needed, then clear
+// the error word and the sums a cut-short launch may have left behind.
+md_status grow_after_overflow(md_handle *h, const Ctl &c)
+{
+    bool grew = false;
+    if (c.max_nn > h->K) {
+        int K = (int)round_up((long long)(c.max_nn * 1.25) + 32, 32);
+        if (K > 65535 || alloc_list(h, K) != MD_OK) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list too long");
+        grew = true;
+    }
+    if (c.max_halo > h->b.hcap) {
+        const int lim = (h->precision == MD_FP32_FIXED) ? 12288 : 8192;   // shared memory per block
+        int hc = (int)round_up((long long)(c.max_halo * 1.25), 128);
+        if (c.max_halo > lim) return fail(h, MD_ERR_LIST_OVERFLOW, "a cell neighbourhood exceeds the halo capacity");
+        h->b.hcap = std::min(hc, lim);
+        h->gen++;
+        grew = true;
+    }
+    if (!grew) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list overflow that no capacity growth covers");
+    int zero = 0;
+    if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
+        return MD_ERR_CUDA;
+    if (h->b.Fq && !cuda_ok(h, cudaMemset(h->b.Fq, 0, sizeof(long long) * 3 * h->S), "clear force sums"))
+        return MD_ERR_CUDA;
+    if (!cuda_ok(h, cudaMemset(h->b.eacc, 0, sizeof(long long) * 4 * (size_t)h->b.nrep), "clear energy sums"))
+        return MD_ERR_CUDA;
+    return MD_OK;
 }
 
 }  // namespace
@@ -677,6 +711,63 @@ md_status md_get_state(md_handle *h, double *x, double *v, void *stream)
     return sync_and_check(h, st);
 }
 
+md_status md_get_checkpoint(md_handle *h, double *x, double *v, double *f, int64_t *step, void *stream)
+{
+    if (!h || !x || !v || !f || !step) return fail(h, MD_ERR_ARG, "md_get_checkpoint: null argument");
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_get_checkpoint before md_set_state");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the force the next step starts from; evaluated now, as md_step would,
+    // when none is stored
+    if (!h->F_valid) {
+        mdk::launch_rebuild_chain(h->b, st);
+        mdk::launch_force(h->b, h->precision, mdk::kModeStore, false, st);
+        if (!cuda_ok(h, cudaGetLastError(), "force launch")) return MD_ERR_CUDA;
+        h->F_valid = true;
+    }
+    double *xs = h->stage, *vs = h->stage + 3 * h->N;
+    const size_t bytes = sizeof(double) * 3 * (size_t)h->N;
+    mdk::launch_get_state(h->b, xs, vs, st);
+    if (!cuda_ok(h, cudaMemcpyAsync(x, xs, bytes, cudaMemcpyDefault, st), "copy positions out") ||
+        !cuda_ok(h, cudaMemcpyAsync(v, vs, bytes, cudaMemcpyDefault, st), "copy velocities out"))
+        return MD_ERR_CUDA;
+    mdk::launch_force_by_id(h->b, xs, 0, st);
+    if (!cuda_ok(h, cudaMemcpyAsync(f, xs, bytes, cudaMemcpyDefault, st), "copy force out")) return MD_ERR_CUDA;
+    md_status s = sync_and_check(h, st);
+    if (s != MD_OK) return s;
+    Ctl c;
+    if ((s = read_ctl(h, &c)) != MD_OK) return s;
+    *step = (int64_t)c.step;
+    return MD_OK;
+}
+
+md_status md_set_checkpoint(md_handle *h, const double *x, const double *v, const double *f, int64_t step,
+                            void *stream)
+{
+    if (!h || !x || !v || !f || step < 0) return fail(h, MD_ERR_ARG, "md_set_checkpoint: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    md_status s = md_set_state(h, x, v, stream);
+    if (s != MD_OK) return s;
+    // the step counter keys the Langevin noise: the resumed run draws the
+    // numbers the uninterrupted one would have drawn
+    const long long stp = (long long)step;
+    if (!cuda_ok(h, cudaMemcpyAsync(&h->b.ctl->step, &stp, sizeof(long long), cudaMemcpyHostToDevice, st),
+                 "restore step"))
+        return MD_ERR_CUDA;
+    // sort and build the list now, then put the stored force into the
+    // particles' new slots (the copy goes through the handle's staging buffer)
+    mdk::launch_set_rebuild(h->b, st);
+    mdk::launch_rebuild_chain(h->b, st);
+    double *fs = h->stage;
+    if (!cuda_ok(h, cudaMemcpyAsync(fs, f, sizeof(double) * 3 * (size_t)h->N, cudaMemcpyDefault, st), "copy force in"))
+        return MD_ERR_CUDA;
+    mdk::launch_force_by_id(h->b, fs, 1, st);
+    if (!cuda_ok(h, cudaGetLastError(), "checkpoint launch")) return MD_ERR_CUDA;
+    s = sync_and_check(h, st);
+    if (s != MD_OK) return s;
+    h->F_valid = true;
+    return MD_OK;
+}
+
 md_status md_build_neighbors(md_handle *h, void *stream)
 {
     if (!h) return MD_ERR_ARG;
@@ -692,24 +783,8 @@ md_status md_build_neighbors(md_handle *h, void *stream)
     if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
     if (read_ctl(h, &c) != MD_OK) return MD_ERR_CUDA;
     if ((c.err & mdk::kErrList) && c.err == mdk::kErrList) {
-        if (c.max_nn > h->K) {
-            int K = (int)round_up((long long)(c.max_nn * 1.25) + 32, 32);
-            if (K > 65535 || alloc_list(h, K) != MD_OK) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list too long");
-        }
-        if (c.max_halo > h->b.hcap) {
-            const int lim = (h->precision == MD_FP32_FIXED) ? 12288 : 8192;   // shared memory per block
-            int hc = (int)round_up((long long)(c.max_halo * 1.25), 128);
-            if (c.max_halo > lim) return fail(h, MD_ERR_LIST_OVERFLOW, "a cell neighbourhood exceeds the halo capacity");
-            h->b.hcap = std::min(hc, lim);
-            h->gen++;
-        }
-        int zero = 0;
-        if (!cuda_ok(h, cudaMemcpy(&h->b.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear error"))
-            return MD_ERR_CUDA;
-        if (h->b.Fq && !cuda_ok(h, cudaMemset(h->b.Fq, 0, sizeof(long long) * 3 * h->S), "clear force sums"))
-            return MD_ERR_CUDA;
-        if (!cuda_ok(h, cudaMemset(h->b.eacc, 0, sizeof(long long) * 4 * (size_t)h->b.nrep), "clear energy sums"))
-            return MD_ERR_CUDA;
+        md_status g = grow_after_overflow(h, c);
+        if (g != MD_OK) return g;
         // the overflowing build still sorted the state; build again with the larger capacities
         mdk::launch_set_rebuild(h->b, st);
         mdk::launch_rebuild_chain(h->b, st);
@@ -745,12 +820,11 @@ md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *
     return MD_OK;
 }
 
-md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream)
+}  // extern "C"
+
+// The kernel sequence of md_step (asynchronous).
+static md_status step_launch(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream)
 {
-    if (!h || nsteps < 0 || thermo_every < 0 || (thermo_every > 0 && !thermo_out))
-        return fail(h, MD_ERR_ARG, "md_step: bad arguments");
-    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_step before md_set_state");
-    if (nsteps == 0) return MD_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int nrep = h->b.nrep;
     const long long nrec = thermo_every > 0 ? nsteps / thermo_every : 0;
@@ -797,6 +871,85 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
         !cuda_ok(h, cudaMemcpyAsync(thermo_out, h->thermo_stage, sizeof(double) * nrec * 3 * nrep, cudaMemcpyDefault, st),
                  "copy thermo out"))
         return MD_ERR_CUDA;
+    return MD_OK;
+}
+
+// The rest of an md_step call after an overflowing rebuild: the state holds
+// x at the step t_start of the call (counted from its start) and the
+// half-step velocity before it, its force not yet evaluated.  Rebuilds the
+// list there, then runs the fused force + update of steps t_start ..
+// nsteps - 1 and the final force, with their energy records in place.
+static md_status step_resume(md_handle *h, int t_start, int32_t nsteps, int32_t thermo_every, cudaStream_t st)
+{
+    Bufs b = h->b;
+    const int nrep = b.nrep;
+    mdk::launch_set_rebuild(b, st);
+    for (int t = t_start; t <= nsteps; ++t) {
+        const bool rec = thermo_every > 0 && (t % thermo_every) == 0;
+        b.thermo = rec ? h->thermo_stage + (long long)(t / thermo_every - 1) * 3 * nrep : nullptr;
+        mdk::launch_rebuild_chain(b, st);
+        mdk::launch_force(b, h->precision, t < nsteps ? mdk::kModeFused : mdk::kModeFinal, rec, st);
+    }
+    return cuda_ok(h, cudaGetLastError(), "step launch") ? MD_OK : MD_ERR_CUDA;
+}
+
+extern "C" {
+
+md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *thermo_out, void *stream)
+{
+    if (!h || nsteps < 0 || thermo_every < 0 || (thermo_every > 0 && !thermo_out))
+        return fail(h, MD_ERR_ARG, "md_step: bad arguments");
+    if (!h->state_set) return fail(h, MD_ERR_ARG, "md_step before md_set_state");
+    if (nsteps == 0) return MD_OK;
+    if (!h->recover) return step_launch(h, nsteps, thermo_every, thermo_out, stream);
+    // recovery: the step counter at the start of the call, then the call,
+    // then (after a list or halo overflow) growth and the rest of the call
+    cudaStream_t st = (cudaStream_t)stream;
+    md_status s = sync_and_check(h, st);
+    if (s != MD_OK) return s;
+    Ctl c;
+    if ((s = read_ctl(h, &c)) != MD_OK) return s;
+    const long long step0 = c.step;
+    s = step_launch(h, nsteps, thermo_every, thermo_out, stream);
+    if (s != MD_OK) return s;
+    for (int attempt = 0;; ++attempt) {
+        if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
+        if ((s = read_ctl(h, &c)) != MD_OK) return s;
+        if (c.err != mdk::kErrList || attempt == 4) return status_of(h, c.err);
+        if ((s = grow_after_overflow(h, c)) != MD_OK) return s;
+        h->recoveries += 1;
+        const long long done = c.step - step0;   // drifts completed before the failing rebuild
+        if (done <= 0) {
+            // the rebuild before the first drift failed: the whole call again
+            // (that build cleared the rebuild flag, so it is set again)
+            mdk::launch_set_rebuild(h->b, st);
+            h->F_valid = false;
+            s = step_launch(h, nsteps, thermo_every, thermo_out, stream);
+        } else {
+            s = step_resume(h, (int)done, nsteps, thermo_every, st);
+            const long long nrec = thermo_every > 0 ? nsteps / thermo_every : 0;
+            if (s == MD_OK && nrec > 0 &&
+                !cuda_ok(h, cudaMemcpyAsync(thermo_out, h->thermo_stage, sizeof(double) * nrec * 3 * h->b.nrep,
+                                            cudaMemcpyDefault, st), "copy thermo out"))
+                s = MD_ERR_CUDA;
+            h->F_valid = true;
+        }
+        if (s != MD_OK) return s;
+    }
+}
+
+md_status md_check_wait_timeout(md_handle *h, int32_t polls, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    if (polls < 1 || polls > 65536) return fail(h, MD_ERR_ARG, "md_check_wait_timeout: polls outside 1..65536");
+    mdk::launch_wait_selftest(h->b, polls, (cudaStream_t)stream);
+    return cuda_ok(h, cudaGetLastError(), "self-test launch") ? MD_OK : MD_ERR_CUDA;
+}
+
+md_status md_set_recovery(md_handle *h, int32_t enable)
+{
+    if (!h) return MD_ERR_ARG;
+    h->recover = enable != 0;
     return MD_OK;
 }
 
@@ -853,6 +1006,7 @@ md_status md_get_stats(md_handle *h, md_stats *out)
     out->max_halo = c.max_halo;
     out->halo_capacity = h->b.hcap;
     out->tile_size = h->b.tile_max;
+    out->recoveries = h->recoveries;
     return status_of(h, c.err);
 }
 
@@ -906,9 +1060,10 @@ static md_status adj_load(md_handle *h, const double *x, cudaStream_t st)
     return cuda_ok(h, cudaGetLastError(), "reload launch") ? MD_OK : MD_ERR_CUDA;
 }
 
-md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, double *dL_dsigma, void *stream)
+md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, const double *dL_deuw, double *dL_deps,
+                      double *dL_dsigma, void *stream)
 {
-    if (!h || !dL_deuw || !dL_deps || !dL_dsigma) return fail(h, MD_ERR_ARG, "md_backward: null argument");
+    if (!h || !dL_deps || !dL_dsigma) return fail(h, MD_ERR_ARG, "md_backward: null argument");
     if (!h->ad_ready) return fail(h, MD_ERR_ARG, "md_backward without a recorded md_forward");
     cudaStream_t st = (cudaStream_t)stream;
     const int nrep = h->b.nrep;
@@ -929,8 +1084,9 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
     double *lx = h->ad_work, *lv = lx + n3, *hv = lv + n3;
     double *coef = h->ad_small, *g = coef + 4 * nrep, *sums = g + 4 * nrep;
     // loss weights (dL/dU, dL/dK, dL/dW) per replica, from host or device memory
-    std::vector<double> in(3 * nrep), cf(12 * nrep, 0.0);
-    if (!cuda_ok(h, cudaMemcpy(in.data(), dL_deuw, sizeof(double) * 3 * nrep, cudaMemcpyDefault), "read dL_deuw"))
+    std::vector<double> in(3 * nrep, 0.0), cf(12 * nrep, 0.0);
+    if (dL_deuw &&
+        !cuda_ok(h, cudaMemcpy(in.data(), dL_deuw, sizeof(double) * 3 * nrep, cudaMemcpyDefault), "read dL_deuw"))
         return MD_ERR_CUDA;
     for (int r = 0; r < nrep; ++r)
         for (int q = 0; q < 3; ++q) cf[4 * r + q] = in[3 * r + q];
@@ -942,6 +1098,17 @@ md_status md_backward(md_handle *h, const double *dL_deuw, double *dL_deps, doub
     if (s != MD_OK) return s;
     mdk::launch_adj_loss(h->b, coef, lx, lv, sums, st);
     mdk::launch_adj_finish_loss(h->b, sums, coef, g, st);
+    // the loss's own gradients in the final positions and velocities join
+    // the terminal adjoints (staged through the handle's buffer: they may be
+    // host memory)
+    if (dL_dx || dL_dv) {
+        double *gx = h->stage, *gv = h->stage + n3;
+        if (dL_dx && !cuda_ok(h, cudaMemcpyAsync(gx, dL_dx, sizeof(double) * n3, cudaMemcpyDefault, st), "read dL_dx"))
+            return MD_ERR_CUDA;
+        if (dL_dv && !cuda_ok(h, cudaMemcpyAsync(gv, dL_dv, sizeof(double) * n3, cudaMemcpyDefault, st), "read dL_dv"))
+            return MD_ERR_CUDA;
+        mdk::launch_adj_add(n3, lx, lv, dL_dx ? gx : nullptr, dL_dv ? gv : nullptr, st);
+    }
     // reverse through the steps, one checkpoint segment at a time (last first)
     if (T > 0) {
         const int nseg = (T + k - 1) / k;

@@ -287,11 +287,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 
 // Wait for the completion of the barrier phase with the given parity, giving
-// up after a bounded number of polls (each may suspend the thread briefly;
-// in all about a second).  Returns false on giving up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// up after `polls` polls (each may suspend the thread briefly; the default of
+// 2^20 polls is about a second in all).  Returns false on giving up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int polls = (1 << 20))
 {
-    for (int it = 0; it < (1 << 20); ++it) {
+    for (int it = 0; it < polls; ++it) {
         unsigned done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -424,10 +424,14 @@ void launch_set_rebuild(const Bufs &b, cudaStream_t st);
 // graph conditionals: set `handle` to (ctl->rebuild != 0) (what = 0) or (ctl->steps_left > 0) (what = 1)
 void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_t st);
 void launch_set_steps(const Bufs &b, long long left, cudaStream_t st);
+// one block waiting on a barrier that nothing completes, `polls` polls at most
+void launch_wait_selftest(const Bufs &b, int polls, cudaStream_t st);
 void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, double scale, double *g,
                     cudaStream_t st);
 void launch_adj_loss(const Bufs &b, const double *coef, double *lx, double *lv, double *sums, cudaStream_t st);
 void launch_adj_finish_loss(const Bufs &b, const double *sums, const double *coef, double *g, cudaStream_t st);
 void launch_adj_update(long long n3, double *lx, double *lv, const double *hv, double c, double dt, cudaStream_t st);
+// lx += gx, lv += gv (either may be null)
+void launch_adj_add(long long n3, double *lx, double *lv, const double *gx, const double *gv, cudaStream_t st);
 
 }  // namespace mdk

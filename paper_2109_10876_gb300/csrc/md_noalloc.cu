@@ -1,15 +1,16 @@
-// Force evaluation that allocates no memory, for callers that cannot allocate
-// device memory: code that runs while a CUDA stream is being captured into a
-// graph (cudaMalloc is not allowed there), or a host framework that owns all
-// device memory through its own allocator.  The caller passes device inputs
-// and outputs; the only scratch, the per-block energy partials, lives in a
-// file-scope device array that every GPU loading this library holds until
-// the process exits.
+// Force evaluation that allocates no memory, for callers that cannot call
+// cudaMalloc: a host framework that owns every byte of device memory through
+// its own pool and forbids other allocators, or a process whose device
+// memory is already committed to a fixed budget.  The caller passes device
+// inputs and outputs; the only scratch, the per-block energy partials, lives
+// in a file-scope device array that every GPU loading this library holds
+// until the process exits.
 //
-// The pair arithmetic is the library's (shifted LJ / WCA under r < r_cut,
-// minimum image, FP32 pairs with 64-bit fixed-point sums or FP64), summed
-// directly over all pairs, without cells or Verlet lists: O(N^2), meant for
-// systems of up to kNoAllocMaxN particles.
+// The pair arithmetic is the library's non-bonded term (shifted LJ / WCA
+// under r < r_cut, minimum image, FP32 pairs with 64-bit fixed-point sums or
+// FP64), summed directly over all pairs, without cells or Verlet lists:
+// O(N^2), meant for systems of up to kNoAllocMaxN particles.  Bonded terms
+// (FENE, angles) are not evaluated here.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -52,6 +53,7 @@ struct DirectParams {
     float qs[3];
     double eps, sigma, rc2, vshift;
     float eps24_f, eps4_f, sig2_f, vshift_f, rc2_lo, rc2_hi;
+    float fmax2;   // FP32: smallest r^2 at which a pair-force component stays inside the fixed-point range
 };
 
 __device__ __noinline__ double r2_exact(const double *x, long long n, long long i, long long j, const double *L)
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_direct(DirectParams p, const doubl
     unsigned hx = 0, lx = 0, hy = 0, ly = 0, hz = 0, lz = 0, hu = 0, lu = 0, hw = 0, lw = 0;
     double F[3] = {0.0, 0.0, 0.0}, U = 0.0, W = 0.0;
     unsigned qi[3] = {0u, 0u, 0u};
+    bool tooclose = false;   // FP32: a pair closer than the fixed-point range allows (or coincident)
     if (PREC == 1 && real) {
         const double xyz[3] = {xi, yi, zi};
         for (int k = 0; k < 3; ++k) qi[k] = (unsigned)(__double2ll_rn(xyz[k] * p.to_q[k]) & 0xffffffffLL);
@@ -101,6 +104,9 @@ __global__ void __launch_bounds__(kThreads) k_direct(DirectParams p, const doubl
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < p.rc2_hi)) continue;
                 if (!(r2 < p.rc2_lo) && !(r2_exact(x, p.n, i, j, p.L) < p.rc2)) continue;
+                // the two-integer split is exact only for |f d| < 2^21: such a
+                // pair (and r = 0) poisons this particle's results instead
+                if (r2 < p.fmax2) { tooclose = true; continue; }
                 const float ir2 = 1.0f / r2;
                 const float s2 = p.sig2_f * ir2, s6 = s2 * s2 * s2;
                 const float fs = p.eps24_f * s6 * (2.0f * s6 - 1.0f) * ir2;
@@ -129,6 +135,10 @@ __global__ void __launch_bounds__(kThreads) k_direct(DirectParams p, const doubl
         F[2] = fix_value(hz, lz);
         U = fix_value(hu, lu);
         W = fix_value(hw, lw);
+        if (tooclose) {
+            const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+            F[0] = F[1] = F[2] = U = W = qnan;
+        }
     }
     if (real)
         for (int k = 0; k < 3; ++k) f[k * p.n + i] = F[k];
@@ -170,7 +180,9 @@ __global__ void __launch_bounds__(kThreads) k_direct_sum(long long n, int nblk, 
 }
 
 // Device address of the scratch array, looked up once per device with that
-// device current (in host code the array's name is only a host-side stand-in).
+// device current (in host code the array's name is only a host-side stand-in)
+// and kept for the life of the process: a cudaDeviceReset, which ends the
+// device's primary context, leaves a stale address behind.
 std::mutex g_mutex;
 double *g_scratch_ptr[64] = {nullptr};
 
@@ -243,6 +255,18 @@ extern "C" md_status md_compute_forces_noalloc(const double *x, const double *v,
     const double band = 2.0 * rc * std::sqrt(3.0) * Lmax / 4294967296.0 + std::ldexp(1.0, -16) * rc * rc;
     p.rc2_lo = (float)(rc * rc - band);
     p.rc2_hi = (float)(rc * rc + band);
+    {
+        // smallest r at which the pair force 24 eps (2 (s/r)^12 - (s/r)^6) / r
+        // stays below 0.9 x 2^21, by bisection (the force falls with r there)
+        double lo = 1e-3 * sigma, hi = rc;
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            const double m6 = std::pow(sigma / mid, 6.0);
+            const double fm = 24.0 * eps * (2.0 * m6 * m6 - m6) / mid;
+            if (fm > std::ldexp(1.0, 21) * 0.9) lo = mid; else hi = mid;
+        }
+        p.fmax2 = (float)(hi * hi);
+    }
     double *scratch = nullptr;
     cudaError_t e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) {

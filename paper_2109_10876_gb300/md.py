@@ -79,6 +79,7 @@ class md_stats(C.Structure):
         ("max_halo", C.c_int32),
         ("halo_capacity", C.c_int32),
         ("tile_size", C.c_int32),
+        ("recoveries", C.c_int64),
     ]
 
 
@@ -111,7 +112,15 @@ _lib.md_get_stats.argtypes = [_H, C.POINTER(md_stats)]
 _lib.md_forward.restype = C.c_int
 _lib.md_forward.argtypes = [_H, C.c_int32, C.c_int32, _vp, _vp]
 _lib.md_backward.restype = C.c_int
-_lib.md_backward.argtypes = [_H, _vp, _vp, _vp, _vp]
+_lib.md_backward.argtypes = [_H, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.md_get_checkpoint.restype = C.c_int
+_lib.md_get_checkpoint.argtypes = [_H, _vp, _vp, _vp, C.POINTER(C.c_int64), _vp]
+_lib.md_set_checkpoint.restype = C.c_int
+_lib.md_set_checkpoint.argtypes = [_H, _vp, _vp, _vp, C.c_int64, _vp]
+_lib.md_set_recovery.restype = C.c_int
+_lib.md_set_recovery.argtypes = [_H, C.c_int32]
+_lib.md_check_wait_timeout.restype = C.c_int
+_lib.md_check_wait_timeout.argtypes = [_H, C.c_int32, _vp]
 _lib.md_autotune.restype = C.c_int
 _lib.md_autotune.argtypes = [_H, C.c_int32, C.POINTER(C.c_int32), _vp]
 _lib.md_set_tile_size.restype = C.c_int
@@ -126,6 +135,8 @@ _lib.md_compute_forces_noalloc.restype = C.c_int
 _lib.md_compute_forces_noalloc.argtypes = [_vp, _vp, C.c_int64, C.POINTER(C.c_double), C.c_double, C.c_double,
                                            C.c_double, C.c_int32, C.c_int32, C.c_double, _vp, _vp,
                                            C.c_char_p, C.c_int32, _vp]
+_lib.md_probe_fp64_fma.restype = C.c_int
+_lib.md_probe_fp64_fma.argtypes = [C.c_int64, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]
 _lib.md_last_error.restype = C.c_char_p
 _lib.md_last_error.argtypes = [_H]
 
@@ -263,8 +274,30 @@ def md_forward(h, nsteps, ckpt_every, euw_out=None, stream=None):
     return _check(h.ptr, _lib.md_forward(h.ptr, int(nsteps), int(ckpt_every), _ptr(euw_out), _stream(stream)))
 
 
-def md_backward(h, dL_deuw, dL_deps, dL_dsigma, stream=None):
-    return _check(h.ptr, _lib.md_backward(h.ptr, _ptr(dL_deuw), _ptr(dL_deps), _ptr(dL_dsigma), _stream(stream)))
+def md_backward(h, dL_dx, dL_dv, dL_deuw, dL_deps, dL_dsigma, stream=None):
+    """md_backward: dL_dx, dL_dv ((3, N) or None) and dL_deuw ((R, 3) or None)
+    in; dL_deps, dL_dsigma (R each) out."""
+    return _check(h.ptr, _lib.md_backward(h.ptr, _ptr(dL_dx), _ptr(dL_dv), _ptr(dL_deuw), _ptr(dL_deps),
+                                          _ptr(dL_dsigma), _stream(stream)))
+
+
+def md_get_checkpoint(h, x, v, f, stream=None):
+    """md_get_checkpoint: fills x, v, f ((3, N) each); returns the step counter."""
+    step = C.c_int64(0)
+    _check(h.ptr, _lib.md_get_checkpoint(h.ptr, _ptr(x), _ptr(v), _ptr(f), C.byref(step), _stream(stream)))
+    return step.value
+
+
+def md_set_checkpoint(h, x, v, f, step, stream=None):
+    return _check(h.ptr, _lib.md_set_checkpoint(h.ptr, _ptr(x), _ptr(v), _ptr(f), int(step), _stream(stream)))
+
+
+def md_set_recovery(h, enable=True):
+    return _check(h.ptr, _lib.md_set_recovery(h.ptr, 1 if enable else 0))
+
+
+def md_check_wait_timeout(h, polls=1000, stream=None):
+    return _check(h.ptr, _lib.md_check_wait_timeout(h.ptr, int(polls), _stream(stream)))
 
 
 def md_export_pairs(h, pairs_out, capacity, stream=None):
@@ -324,6 +357,15 @@ def md_compute_forces_noalloc(x, v, n, box, f_out, euw_out=None, eps=1.0, sigma=
     if st != MD_OK:
         raise MDError(st, buf.value.decode())
     return st
+
+
+def md_probe_fp64_fma(iters=100000, blocks_per_sm=4, stream=None):
+    """md_probe_fp64_fma (include/md_probe.h): measured FP64 FMA rate, returns (TFLOP/s, ms)."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    st = _lib.md_probe_fp64_fma(int(iters), int(blocks_per_sm), C.byref(tf), C.byref(ms), _stream(stream))
+    if st != 0:
+        raise MDError(MD_ERR_CUDA if st == -2 else MD_ERR_ARG, "md_probe_fp64_fma failed")
+    return tf.value, ms.value
 
 
 def md_last_error(h):

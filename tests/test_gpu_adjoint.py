@@ -51,13 +51,60 @@ def test_backward_matches_oracle_adjoint(md, precision, T, k, tol):
     md.md_forward(h, T, k, euw)
     c = np.array([loss_coefs(n, b) for n, b in zip(sizes, boxes)])
     ge, gs = np.zeros(2), np.zeros(2)
-    md.md_backward(h, c, ge, gs)
+    md.md_backward(h, None, None, c, ge, gs)
     for r, (x, v, box) in enumerate(reps):
         s = oracle.System(len(x), box, rc=2.5, dt=0.005)
         e_ref, ge_ref, gs_ref, _, _ = oracle.vv_adjoint(s, x, v, T, *c[r])
         np.testing.assert_allclose(euw[r], e_ref, rtol=1e-9 if precision == 0 else 1e-4)
         assert ge[r] == pytest.approx(ge_ref, rel=tol)
         assert gs[r] == pytest.approx(gs_ref, rel=tol)
+
+
+@pytest.mark.parametrize("precision,T,k,tol", [(0, 30, 10, 1e-8), (1, 7, 3, 2e-4)])
+def test_backward_of_final_state_loss_matches_oracle(md, precision, T, k, tol):
+    """A loss on the end point of the trajectory as well as on its energies,
+    L = c . (U, K, W) + gx . x_T + gv . v_T per replica: md_backward with
+    dL_dx = gx and dL_dv = gv equals the oracle's reverse pass with the same
+    terminal adjoints."""
+    reps = two_replicas()
+    sizes = [len(r[0]) for r in reps]
+    boxes = np.array([r[2] for r in reps])
+    N = sum(sizes)
+    rng = np.random.default_rng(90)
+    gx, gv = rng.normal(size=(N, 3)), rng.normal(size=(N, 3))
+    h = md.md_create(sizes, boxes, eps=[1.0, 1.0], sigma=[1.0, 1.0], precision=precision)
+    md.md_set_state(h, dev(np.concatenate([r[0] for r in reps])), dev(np.concatenate([r[1] for r in reps])))
+    md.md_build_neighbors(h)
+    md.md_forward(h, T, k, None)
+    c = np.array([loss_coefs(n, b) for n, b in zip(sizes, boxes)])
+    ge, gs = np.zeros(2), np.zeros(2)
+    md.md_backward(h, dev(gx), dev(gv), c, ge, gs)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for r, (x, v, box) in enumerate(reps):
+        a, b = off[r], off[r + 1]
+        s = oracle.System(len(x), box, rc=2.5, dt=0.005)
+        _, ge_ref, gs_ref, _, _ = oracle.vv_adjoint(s, x, v, T, *c[r], gx=gx[a:b], gv=gv[a:b])
+        assert ge[r] == pytest.approx(ge_ref, rel=tol)
+        assert gs[r] == pytest.approx(gs_ref, rel=tol)
+
+
+def test_backward_end_point_loss_only(md):
+    """dL_deuw = NULL: a loss on the final positions and velocities alone
+    (host arrays), FP64 forward, against the oracle."""
+    x, v, box = two_replicas()[1]
+    n = len(x)
+    rng = np.random.default_rng(91)
+    gx, gv = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    h = md.md_create(n, box, precision=0)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    md.md_forward(h, 12, 4, None)
+    ge, gs = np.zeros(1), np.zeros(1)
+    md.md_backward(h, np.ascontiguousarray(gx.T), np.ascontiguousarray(gv.T), None, ge, gs)
+    s = oracle.System(n, box, rc=2.5, dt=0.005)
+    _, ge_ref, gs_ref, _, _ = oracle.vv_adjoint(s, x, v, 12, 0.0, 0.0, 0.0, gx=gx, gv=gv)
+    assert ge[0] == pytest.approx(ge_ref, rel=1e-8)
+    assert gs[0] == pytest.approx(gs_ref, rel=1e-8)
 
 
 def test_backward_matches_central_differences(md):
@@ -78,13 +125,41 @@ def test_backward_matches_central_differences(md):
 
     h0, _ = run(1.0, 1.0)
     ge, gs = np.zeros(1), np.zeros(1)
-    md.md_backward(h0, c, ge, gs)
+    md.md_backward(h0, None, None, c, ge, gs)
     he = 1e-4
     fe = (run(1 + he, 1.0)[1] - run(1 - he, 1.0)[1]) / (2 * he)
     hs = 1e-6
     fs = (run(1.0, 1 + hs)[1] - run(1.0, 1 - hs)[1]) / (2 * hs)
     assert ge[0] == pytest.approx(fe, rel=1e-4)
     assert gs[0] == pytest.approx(fs, rel=1e-4)
+
+
+def test_autograd_face_end_point_loss(md):
+    """torch.autograd through ensemble_run with a loss on the final positions
+    and velocities as well as on the energies: the gradients are the oracle's."""
+    from paper_2109_10876_gb300 import adjoint
+    reps = two_replicas()
+    sizes = [len(r[0]) for r in reps]
+    boxes = np.array([r[2] for r in reps])
+    X = np.concatenate([r[0] for r in reps])
+    V = np.concatenate([r[1] for r in reps])
+    spec = dict(sizes=sizes, box=boxes, x=dev(X), v=dev(V), nsteps=10, ckpt_every=5, precision=0)
+    rng = np.random.default_rng(92)
+    wx = torch.tensor(rng.normal(size=(3, len(X))), device="cuda")
+    wv = torch.tensor(rng.normal(size=(3, len(X))), device="cuda")
+    eps = torch.tensor([1.0, 1.02], dtype=torch.float64, requires_grad=True)
+    sig = torch.tensor([1.0, 0.99], dtype=torch.float64, requires_grad=True)
+    euw, xT, vT = adjoint.ensemble_run(eps, sig, spec)
+    loss = adjoint.mean_energy_plus_pressure(euw, sizes, boxes).sum() + (wx * xT).sum() + (wv * vT).sum()
+    loss.backward()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for r, (x, v, box) in enumerate(reps):
+        a, b = off[r], off[r + 1]
+        s = oracle.System(len(x), box, eps=float(eps[r]), sigma=float(sig[r]), rc=2.5 * float(sig[r]), dt=0.005)
+        _, ge_ref, gs_ref, _, _ = oracle.vv_adjoint(s, x, v, 10, *loss_coefs(len(x), box),
+                                                    gx=wx.cpu().numpy().T[a:b], gv=wv.cpu().numpy().T[a:b])
+        assert float(eps.grad[r]) == pytest.approx(ge_ref, rel=1e-8)
+        assert float(sig.grad[r]) == pytest.approx(gs_ref, rel=1e-8)
 
 
 def test_autograd_face(md):

@@ -384,7 +384,7 @@ def test_full_size_ensemble_forces_and_adjoint(md):
     for pot, which, hrel in ((md.MD_LJ, 0, 1e-8), (md.MD_WCA, 1, 1e-6)):
         h0, _ = forward(eps, sig, pot, keep=True)
         ge, gs = np.zeros(R), np.zeros(R)
-        md.md_backward(h0, coef, ge, gs)
+        md.md_backward(h0, None, None, coef, ge, gs)
         h0.destroy()
         if which == 0:
             fd = (forward(eps * (1 + hrel), sig, pot) - forward(eps * (1 - hrel), sig, pot)) / (2 * hrel * eps)
