@@ -44,7 +44,15 @@ FORCE_FIXED_BYTES = 16 + 4 + 48 + 48 + 16 + 16
 # interacting pair adds 1/r^2 1, (sigma/r)^2 1, ^6 2, force scalar 4, force
 # accumulation 6 (26 in all)
 FP64_OPS_OUT, FP64_OPS_IN = 12, 26
-FP64_NOMINAL_TFLOPS = 1.25      # GB300 nominal FP64 rate (no measured FP64 peak on this machine)
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 nominal FP64 rate, context only: the roofline uses the measured probe
+# the algorithmic HBM bytes of one force + integrate step per particle, full
+# Verlet list, rebuild excluded, as the scope table of the method counts them
+# (a 4-byte index per list entry at 82.4 entries, twice the paper's 41.2
+# neighbours per particle): own float4 16, list offset 4, list indices 329.6,
+# force writes 24, integrator (F read 24, x r/w 48, v r/w 48, float4 write 16,
+# x_ref read 24) 160
+SCOPE_BYTES_FULL = 16 + 4 + 82.4 * 4 + 24 + 160
+SCOPE_BYTES_HALF = 16 + 4 + 41.2 * 4 + 24 + 160
 # the half list adds, per particle, the fixed-point force sums: 24 B written
 # by the pair pass (the atomics' net result), 24 B read and 24 B cleared by
 # the integrating pass
@@ -278,7 +286,7 @@ def ensemble_leg(md, torch, dev, passes=3, nsteps=200, ckpt=20):
         md.md_set_state(h, xt, vt)
         md.md_build_neighbors(h)
         md.md_forward(h, nsteps, ckpt, euw)
-        md.md_backward(h, g, ge, gs)
+        md.md_backward(h, None, None, g, ge, gs)
 
     one()                                   # first use: allocations, untimed
     torch.cuda.synchronize()
@@ -315,34 +323,38 @@ def timed_steps(md, torch, h, steps, stream):
     return e0.elapsed_time(e1), st0, st1, ck
 
 
-def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=None):
+def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=None, steps=None, emit=True):
     # systems with bonds or angle triples add one kernel to each rebuild (the
     # slots of their partners)
     chain_kernels = REBUILD_KERNELS if chain_kernels is None else chain_kernels
+    steps = args.steps if steps is None else steps
     stream = torch.cuda.current_stream()
     md.md_step(h, max(args.warmup, 3))
     md.md_sync(h)
-    ms, st0, st1, ck = timed_steps(md, torch, h, args.steps, stream)
+    ms, st0, st1, ck = timed_steps(md, torch, h, steps, stream)
     rb = st1["rebuilds"] - st0["rebuilds"]
     # a second pass of the same length with per-launch events: where the time goes
     md.md_set_timing(h, True)
-    md.md_step(h, args.steps)
+    md.md_step(h, steps)
     sect_ms, _ = md.md_get_timing(h)
     md.md_set_timing(h, False)
-    line = {"metric": f"{name} particle-steps/s", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+    line = {"metric": f"{name} particle-steps/s", "value": n * steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+fixed64 (f64 integration)", "data": "synthetic",
             "config": dict(extra, particles=n, tile_size=st1["tile_size"]),
-            "rebuilds": rb, "gpu_launches": 2 * args.steps + 3 + chain_kernels * rb,
+            "rebuilds": rb, "steps_per_rebuild": steps / max(rb, 1),
+            "gpu_launches": 2 * steps + 3 + chain_kernels * rb,
             "mean_list_len": st1["list_entries"] / n, "max_list_len": st1["max_list_len"],
             "max_cell_occupancy": st1["max_cell_occupancy"], "tiles": st1["n_tiles"],
             "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck,
-            "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / args.steps,
-                                     "force_integrate": sect_ms[md.MD_SECT_FORCE] / args.steps,
-                                     "other": sect_ms[md.MD_SECT_OTHER] / args.steps,
+            "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / steps,
+                                     "force_integrate": sect_ms[md.MD_SECT_FORCE] / steps,
+                                     "other": sect_ms[md.MD_SECT_OTHER] / steps,
                                      "note": "second pass with per-launch events"}}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_melt(md, torch, dev, args):
@@ -432,7 +444,7 @@ def run_rings(md, torch, dev, args):
     h.destroy()
 
 
-def run_slab(md, torch, dev, args):
+def run_slab(md, torch, dev, args, steps=None, emit=True):
     """Liquid/vapour slab: 1,000,000 LJ particles, Lz = 4 Lx = 4 Ly, liquid at
     0.80 in the central quarter of z, vapour at 0.02 elsewhere, random
     sequential placement with minimum separation 0.8, T = 0.8, rc 2.5,
@@ -446,14 +458,15 @@ def run_slab(md, torch, dev, args):
     md.md_build_neighbors(h)
     md.md_autotune(h, 10)
     prep = f"random sequential placement of 1e6 particles: {time.perf_counter() - t0:.1f} s"
-    workload_line(md, torch, dev, args, "liquid/vapour slab", n, h, prep,
-                  {"workload": f"LJ liquid/vapour slab, N = {n}, box {box[0]:.3f} x {box[1]:.3f} x {box[2]:.3f}, "
-                               f"liquid 0.80 / vapour 0.02, T* 0.8, rc 2.5, skin 0.3, dt 0.005, NVE",
-                   "l2": "working set about 160 MB (larger than L2)"})
+    line = workload_line(md, torch, dev, args, "liquid/vapour slab", n, h, prep,
+                         {"workload": f"LJ liquid/vapour slab, N = {n}, box {box[0]:.3f} x {box[1]:.3f} x "
+                                      f"{box[2]:.3f}, liquid 0.80 / vapour 0.02, T* 0.8, rc 2.5, skin 0.3, dt 0.005, NVE",
+                          "l2": "working set about 160 MB (larger than L2)"}, steps=steps, emit=emit)
     h.destroy()
+    return line
 
 
-def run_sphere(md, torch, dev, args):
+def run_sphere(md, torch, dev, args, steps=None, emit=True):
     """Spherical inhomogeneous LJ system (the paper's load-imbalance case):
     2.58 million particles at density 0.8442 in a central sphere of a cubic box
     of edge 271, vacuum around it, Langevin thermostat at T = 0.1 (gamma 0.5),
@@ -468,11 +481,12 @@ def run_sphere(md, torch, dev, args):
     md.md_build_neighbors(h)
     md.md_autotune(h, 10)
     prep = f"fcc sites nearest the centre: {time.perf_counter() - t0:.1f} s"
-    workload_line(md, torch, dev, args, "LJ sphere in vacuum", n, h, prep,
-                  {"workload": f"LJ sphere, N = {n} at rho 0.8442 (radius 90.0) in a cubic box of edge 271, "
-                               f"Langevin T 0.1 (gamma 0.5), rc 2.5, skin 0.3, dt 0.005",
-                   "l2": "working set about 800 MB (larger than L2)"})
+    line = workload_line(md, torch, dev, args, "LJ sphere in vacuum", n, h, prep,
+                         {"workload": f"LJ sphere, N = {n} at rho 0.8442 (radius 90.0) in a cubic box of edge 271, "
+                                      f"Langevin T 0.1 (gamma 0.5), rc 2.5, skin 0.3, dt 0.005",
+                          "l2": "working set about 800 MB (larger than L2)"}, steps=steps, emit=emit)
     h.destroy()
+    return line
 
 
 def run_reference(args, world, rank):
@@ -580,9 +594,11 @@ def main():
     pad = 4
     list_bytes = 2.0 * (mean_nn + (pad - 1) / 2.0)
     bytes_pp = FORCE_FIXED_BYTES + list_bytes + (HALF_SUM_BYTES if half else 0)
+    scope_pp = SCOPE_BYTES_HALF if half else SCOPE_BYTES_FULL
     # the force section holds one fused launch per step (two with the half list)
     force_ms = sect_ms[md.MD_SECT_FORCE] / max(sect_n[md.MD_SECT_FORCE], 1)
-    achieved = n * bytes_pp / (force_ms * 1e-3) / 1e9
+    achieved = n * scope_pp / (force_ms * 1e-3) / 1e9
+    achieved_layout = n * bytes_pp / (force_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     digest = csrc_digest()
     tpp = profiled_traffic(digest)
@@ -605,7 +621,15 @@ def main():
                 "traffic": None if (tpp is None or half) else round(tpp * n),
                 "peak_source": peak_kind,
                 "kernel": "k_pairs_half + k_force<FP32, fused, half>" if half else "k_force<FP32, fused>",
-                "algorithmic_bytes_per_particle": round(bytes_pp, 1),
+                "algorithmic_bytes_per_particle": round(scope_pp, 1),
+                "bytes_note": "force + integrate per particle, " + ("half" if half else "full") +
+                              " list with 4-byte indices at 82.4 entries (twice the paper's 41.2 neighbours), "
+                              "rebuild excluded",
+                "layout_bytes_per_particle": round(bytes_pp, 1),
+                "layout_achieved": round(achieved_layout, 1),
+                "layout_frac": round(achieved_layout / peak, 4),
+                "layout_note": "the bytes this layout needs: 2-byte halo indices at the live mean list length "
+                               "plus padding, 32-bit fixed-point positions",
                 "launch_ms": round(force_ms, 4)}
 
     extras = {}
@@ -675,13 +699,19 @@ def main():
         n_in = 4.0 / 3.0 * math.pi * RC ** 3 * RHO
         ops = n * (n_in * FP64_OPS_IN + max(mean_nn - n_in, 0.0) * FP64_OPS_OUT)
         tf = ops / (ms64 / k64 * 1e-3) / 1e12
+        # the FP64 FMA rate of this GPU, measured by the library's probe (FMA
+        # chains on every SM; 2 flops per FMA)
+        fp64_peak, fp64_ms = md.md_probe_fp64_fma(100000, 4)
         extras["fp64"] = {"value": world * v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
                           "speedup_fp32_fixed_over_fp64": (value / world) / v64,
-                          "pair_tflops": round(tf, 4), "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
-                          "frac_of_nominal_fp64": round(tf / FP64_NOMINAL_TFLOPS, 4),
+                          "roofline": {"bound": "fp64", "achieved": round(tf, 4), "peak": round(fp64_peak, 4),
+                                       "unit": "TFLOP/s", "frac": round(tf / fp64_peak, 4),
+                                       "peak_source": "measured: md_probe_fp64_fma, FP64 FMA chains on every SM "
+                                                      f"({fp64_ms:.1f} ms launch)",
+                                       "nominal_peak": FP64_NOMINAL_TFLOPS},
                           "ops_per_step": ops,
                           "note": "FP64 operations of the pair sums by count per list entry (12 beyond r_cut, 26 "
-                                  "within), against the nominal FP64 rate; the FP64 path also integrates in FP64"}
+                                  "within); the FP64 path also integrates in FP64"}
 
         # ---- the other list form on the same input (Sec. 2.1.2: the half list
         # of Newton's third law against the full list)
@@ -711,6 +741,32 @@ def main():
             "ratio_to_timed_run": vh_ / (value / world),
             "note": "graph-launched steps on the same input; force_ms_per_step from a second pass "
                     "with per-launch events (the half list's force step is two kernels)"}
+
+        # ---- NVE energy over the workload's own 1000 steps from the lattice
+        # (records every step; the first 100 steps hold the lattice's melting)
+        nE = 1000
+        h6 = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
+        md.md_set_tile_size(h6, tile_size)
+        md.md_set_state(h6, xt, vt)
+        md.md_build_neighbors(h6)
+        th6 = torch.zeros(nE, 3, dtype=torch.float64, device=dev)
+        md.md_step(h6, nE, 1, th6)
+        md.md_sync(h6)
+        h6.destroy()
+        E6 = (th6[:, 0] + th6[:, 1]).cpu().numpy()
+        tail = E6[100:]
+        slope = float(np.polyfit(np.arange(len(tail)) * DT, tail / n, 1)[0])
+        extras["nve_1000"] = {"steps": nE, "E0_per_particle": float(E6[0] / n),
+                              "rel_drift": float((E6[-1] - E6[0]) / abs(E6[0])),
+                              "max_rel_dev": float(np.max(np.abs(E6 - E6[0])) / abs(E6[0])),
+                              "rel_drift_steps_100_to_1000": float((E6[-1] - E6[100]) / abs(E6[100])),
+                              "drift_per_particle_per_tau_after_100": slope,
+                              "note": "FP32 pairs + fixed-point sums, FP64 integration; (U + K) recorded every step"}
+
+        # ---- the other workloads of the paper at full size (one GB300 each)
+        kx = max(100, min(args.steps, 500))
+        extras["slab"] = run_slab(md, torch, dev, args, steps=kx, emit=False)
+        extras["sphere"] = run_sphere(md, torch, dev, args, steps=kx, emit=False)
 
         extras["ensemble"] = ensemble_leg(md, torch, dev)
 
