@@ -219,20 +219,25 @@ __global__ void k_bin(Bufs b)
         b.ctl->list_entries = 0;
         b.ctl->max_occ = 0;
     }
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int c = -1;
-    if (s < b.S) {
-        const uint4 p = b.pos[b.ctl->cur][s];
-        if ((int)p.w >= 0) {
-            const Replica &R = b.rep[b.blk_rep[blockIdx.x]];
-            int cx, cy, cz;
-            cell_coords(p, R, cx, cy, cz);
-            c = R.cell_off + (cz * R.ncell[1] + cy) * R.ncell[0] + cx;
-            b.cellid[s] = c;
+    const int cur = b.ctl->cur;
+    // a bounded grid strides over the blocks of kBlock slots (so that a launch
+    // with no rebuild due costs little)
+    for (int blk = blockIdx.x; blk < b.nblk; blk += gridDim.x) {
+        const long long s = (long long)blk * blockDim.x + threadIdx.x;
+        int c = -1;
+        if (s < b.S) {
+            const uint4 p = b.pos[cur][s];
+            if ((int)p.w >= 0) {
+                const Replica &R = b.rep[b.blk_rep[blk]];
+                int cx, cy, cz;
+                cell_coords(p, R, cx, cy, cz);
+                c = R.cell_off + (cz * R.ncell[1] + cy) * R.ncell[0] + cx;
+                b.cellid[s] = c;
+            }
         }
+        const unsigned peers = __match_any_sync(full, c);
+        if (c >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&b.cell_count[c], __popc(peers));
     }
-    const unsigned peers = __match_any_sync(full, c);
-    if (c >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&b.cell_count[c], __popc(peers));
 }
 
 constexpr int kScanThreads = 1024;
@@ -322,16 +327,19 @@ __global__ void k_scatter(Bufs b)
 {
     const unsigned full = 0xffffffffu;
     if (__shfl_sync(full, (int)(!b.ctl->rebuild || b.ctl->err), 0)) return;   // warp-uniform
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    int c = -1;
-    if (s < b.S && (int)b.pos[b.ctl->cur][s].w >= 0) c = b.cellid[s];
-    const unsigned peers = __match_any_sync(full, c);
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (c >= 0 && lane == leader) base = atomicAdd(&b.cell_end[c], __popc(peers));
-    base = __shfl_sync(full, base, leader);
-    if (c >= 0) b.bucket[base + __popc(peers & ((1u << lane) - 1u))] = (int)s;
+    const int cur = b.ctl->cur;
+    for (int blk = blockIdx.x; blk < b.nblk; blk += gridDim.x) {   // bounded grid, as k_bin
+        const long long s = (long long)blk * blockDim.x + threadIdx.x;
+        int c = -1;
+        if (s < b.S && (int)b.pos[cur][s].w >= 0) c = b.cellid[s];
+        const unsigned peers = __match_any_sync(full, c);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (c >= 0 && lane == leader) base = atomicAdd(&b.cell_end[c], __popc(peers));
+        base = __shfl_sync(full, base, leader);
+        if (c >= 0) b.bucket[base + __popc(peers & ((1u << lane) - 1u))] = (int)s;
+    }
 }
 
 // One warp per cell: order the cell's members by (fixed-point x, particle
@@ -359,32 +367,34 @@ __device__ __forceinline__ void reorder_move(const Bufs &b, int cur, int nxt, in
 __global__ void k_reorder(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
-    long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (gw >= b.C) return;
-    int c = (int)gw;
-    int start = b.cell_start[c], end = b.cell_end[c];
-    int n = end - start;
-    if (lane == 0) b.cell_count[c] = 0;   // histogram is clean for the next build
-    int cur = b.ctl->cur, nxt = cur ^ 1;
+    const int lane = threadIdx.x & 31;
+    const int cur = b.ctl->cur, nxt = cur ^ 1;
     const uint4 *pin = b.pos[cur];
-    if (n <= 32) {
-        const bool act = lane < n;
-        const int s = act ? b.bucket[start + lane] : 0;
-        const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
-        const unsigned long long key = act ? order_key(p) : ~0ULL;
-        int rank = 0;
-        for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, key, q) < key);
-        if (act) reorder_move(b, cur, nxt, c, s, start + rank, p);
-        return;
-    }
-    for (int m = lane; m < n; m += 32) {
-        int s = b.bucket[start + m];
-        uint4 p = pin[s];
-        const unsigned long long key = order_key(p);
-        int rank = 0;
-        for (int q = 0; q < n; ++q) rank += (order_key(pin[b.bucket[start + q]]) < key);
-        reorder_move(b, cur, nxt, c, s, start + rank, p);
+    // a bounded grid of warps strides over the cells
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < b.C; gw += nw) {
+        const int c = (int)gw;
+        const int start = b.cell_start[c], end = b.cell_end[c];
+        const int n = end - start;
+        if (lane == 0) b.cell_count[c] = 0;   // histogram is clean for the next build
+        if (n <= 32) {
+            const bool act = lane < n;
+            const int s = act ? b.bucket[start + lane] : 0;
+            const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
+            const unsigned long long key = act ? order_key(p) : ~0ULL;
+            int rank = 0;
+            for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, key, q) < key);
+            if (act) reorder_move(b, cur, nxt, c, s, start + rank, p);
+            continue;
+        }
+        for (int m = lane; m < n; m += 32) {
+            int s = b.bucket[start + m];
+            uint4 p = pin[s];
+            const unsigned long long key = order_key(p);
+            int rank = 0;
+            for (int q = 0; q < n; ++q) rank += (order_key(pin[b.bucket[start + q]]) < key);
+            reorder_move(b, cur, nxt, c, s, start + rank, p);
+        }
     }
 }
 
@@ -723,7 +733,7 @@ __device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, con
 // the two halves run their own ranges side by side.  Candidates whose FP32
 // r^2 lies within rounding of the list radius are set aside and decided
 // afterwards in FP64 from the master positions (rare), appended after the
-// others.  Appends are branch-free: every candidate is written at the lane's
+// others: a lone one directly, several by walking the ranges again.  Appends are branch-free: every candidate is written at the lane's
 // next free row and the row pointer advances only on a hit.  The shared stage
 // has the final [row][particle] layout of the tile's list block; a list that
 // outgrows it is walked again straight into global memory (rare).
@@ -771,7 +781,8 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         unsigned short *col = own ? lst + pp : dummy + lane;
         const int stride = own ? Pt : 0;
         int cnt = 0;
-        bool tie = false;
+        int nband = 0;    // candidates within rounding of the list radius
+        int tie_h = 0;    // the last of them
         for (int r = 0; r < nrng; ++r) {
             const int h1 = rng[half][r][1];
             int h = rng[half][r][0];
@@ -786,8 +797,11 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                 for (int u = 0; u < 4; ++u) {
                     const float r2 = C::sep2(p, pj[u], ry, rz);
                     const int hj = C::index(pj[u], h + u);
-                    const bool in = (r2 < lo) & (HALF ? hj > thr : hj != self);
-                    tie |= (r2 < hi) & !(r2 < lo);
+                    const bool flt = HALF ? hj > thr : hj != self;
+                    const bool in = (r2 < lo) & flt;
+                    const bool band = (r2 < hi) & !(r2 < lo) & flt;
+                    nband += band;
+                    tie_h = band ? hj : tie_h;
                     *q = (unsigned short)C::index(pj[u], h + u);
                     q += in ? stride : 0;
                     cnt += in;
@@ -795,14 +809,30 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             }
             for (; h < h1; ++h) {
                 const float r2 = C::sep2(p, halo[h], ry, rz);
-                const bool in = (r2 < lo) & (HALF ? h > thr : h != self);
-                tie |= (r2 < hi) & !(r2 < lo);
+                const bool flt = HALF ? h > thr : h != self;
+                const bool in = (r2 < lo) & flt;
+                const bool band = (r2 < hi) & !(r2 < lo) & flt;
+                nband += band;
+                tie_h = band ? h : tie_h;
                 col[max(min(cnt, cap - 4), 0) * stride] = (unsigned short)h;
                 cnt += in;
             }
         }
-        // candidates within rounding of the list radius: FP64, appended
-        if (tie && valid) {
+        // candidates within rounding of the list radius: FP64, appended.  The
+        // common case is a single one, settled directly; more than one means
+        // walking the ranges again (rare)
+        const bool tie = nband > 0;
+        if (valid && nband == 1) {
+            int j = -1;
+            for (int r = 0; r < nrng; ++r) {
+                const int a = rng[half][r][0], e = rng[half][r][1];
+                if (tie_h >= a && tie_h < e) j = rng[half][r][2] + (tie_h - a);
+            }
+            if (j >= 0 && r2_fp64(X, b.S, i, j, R.L) < R.rl2) {
+                col[max(min(cnt, cap - 1), 0) * stride] = (unsigned short)tie_h;
+                ++cnt;
+            }
+        } else if (nband > 1 && valid) {
             for (int r = 0; r < nrng; ++r) {
                 const int h0 = rng[half][r][0], h1 = rng[half][r][1], j0 = rng[half][r][2];
                 const int thr = HALF ? i - j0 + h0 : 0;
@@ -862,15 +892,20 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
     }
 }
 
-// Thread 0 arms the staging barrier with the halo's byte count and issues its
-// bulk (TMA) copies: the pieces, contiguous runs of 16-byte positions.
-__device__ __forceinline__ void issue_halo_bulk(const Piece *pc, int np, const uint4 *P, uint4 *halo,
-                                                unsigned long long *bar)
+// The halo pieces (contiguous runs of 16-byte positions) by bulk (TMA)
+// copies, issued by the 32 lanes of one warp in parallel (up to 18 pieces):
+// lane 0 arms the staging barrier with the halo's byte count, then lane q
+// issues piece q.
+__device__ __forceinline__ void issue_halo_bulk_warp(const Piece *pc, int np, const uint4 *P, uint4 *halo,
+                                                     unsigned long long *bar, int lane)
 {
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u);
+    }
+    __syncwarp();
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u);
-    for (int q = 0; q < np; ++q)
-        if (pc[q].n > 0) bulk_g2s(&halo[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, bar);
+    if (lane < np && pc[lane].n > 0) bulk_g2s(&halo[pc[lane].hoff], &P[pc[lane].slot0], (unsigned)pc[lane].n * 16u, bar);
 }
 
 __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
@@ -928,11 +963,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
             continue;
         }
         // the halo pieces (contiguous runs of 16-byte positions) by bulk (TMA)
-        // copies issued by one thread; every thread waits on the barrier
-        if (threadIdx.x == 0) {
-            s_next = t_next;
-            if (!issued) issue_halo_bulk(pc, s_np, P, halo, &s_mbar);
-        }
+        // copies issued by the first warp; every thread waits on the barrier
+        if (threadIdx.x == 0) s_next = t_next;
+        if (threadIdx.x < 32 && !issued) issue_halo_bulk_warp(pc, s_np, P, halo, &s_mbar, threadIdx.x);
         const bool late = !mbar_wait(&s_mbar, phase);
         phase ^= 1u;
         if (__syncthreads_or(late)) {   // a bulk copy never completed: stop, report
@@ -971,15 +1004,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
         __syncthreads();
         // the halo is free: the next tile's halo copies go out now and arrive
         // while this tile's lists are copied out
-        int issued_next = 0;   // thread 0
-        if (threadIdx.x == 0) {
-            b.tiles[t].kmax = s_kmax;
-            if (pref) {
-                const int npn = s_npb[buf ^ 1];
-                if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
-                    issue_halo_bulk(pcb[buf ^ 1], npn, P, halo, &s_mbar);
-                    issued_next = 1;
-                }
+        int issued_next = 0;   // the first warp (thread 0 publishes it)
+        if (threadIdx.x == 0) b.tiles[t].kmax = s_kmax;
+        if (threadIdx.x < 32 && pref) {
+            const int npn = s_npb[buf ^ 1];
+            if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
+                issue_halo_bulk_warp(pcb[buf ^ 1], npn, P, halo, &s_mbar, threadIdx.x);
+                issued_next = 1;
             }
         }
         // the staged rows are the start of the tile's list block: one
@@ -1110,21 +1141,35 @@ static int list_grid(size_t smem)
     return grid;
 }
 
+// blocks of the bounded-grid chain kernels: 16 per SM, at most `need`
+static unsigned chain_grid(long long need)
+{
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 1;
+    }
+    const long long cap = 16LL * nsm;
+    return (unsigned)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
 void launch_rebuild_chain(const Bufs &b, cudaStream_t st)
 {
-    k_bin<<<b.nblk, kBlock, 0, st>>>(b);
+    k_bin<<<chain_grid(b.nblk), kBlock, 0, st>>>(b);
     const unsigned nsb = (unsigned)((b.C + kScanBlock - 1) / kScanBlock);
     k_scan_sum<<<nsb, kScanBlock, 0, st>>>(b);
     k_scan_top<<<1, kScanThreads, 0, st>>>(b);
     k_scan_write<<<nsb, kScanBlock, 0, st>>>(b);
-    k_scatter<<<b.nblk, kBlock, 0, st>>>(b);
-    k_reorder<<<blocks_for((long long)b.C * 32, 256), 256, 0, st>>>(b);
+    k_scatter<<<chain_grid(b.nblk), kBlock, 0, st>>>(b);
+    k_reorder<<<chain_grid(blocks_for((long long)b.C * 32, 256)), 256, 0, st>>>(b);
     const long long nt = b.n_bond_ent > b.n_ang_ent ? b.n_bond_ent : b.n_ang_ent;
     if (nt > 0) k_topology_slots<<<blocks_for(nt, 256), 256, 0, st>>>(b);
     k_tile_count<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
     k_tile_scan<<<1, kScanThreads, 0, st>>>(b);
     k_tile_write<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
-    k_tile_pieces<<<(unsigned)std::min<long long>(blocks_for(b.C, kTileWarps), 4096), 32 * kTileWarps, 0, st>>>(b);
+    k_tile_pieces<<<chain_grid(blocks_for(b.C, kTileWarps)), 32 * kTileWarps, 0, st>>>(b);
     const size_t smem = list_smem_bytes(b.hcap);
     k_build_list<<<list_grid(smem), kBlock, smem, st>>>(b);
 }

@@ -631,20 +631,27 @@ __device__ __forceinline__ void angle_term(const Real b1[3], const Real b2[3], R
 // the neighbour positions read from the tile's halo in shared memory, then
 // the velocity-Verlet update of that particle.  Persistent blocks take tiles
 // from a work counter.
-// Thread 0 arms the staging barrier with the tile's byte count and issues
-// its bulk (TMA) copies: the halo pieces (contiguous runs of 16-byte
-// positions) and, if it fits the stage, the list block (64-byte aligned, read
-// rounded up to 16 bytes; the list and the stage carry that slack).
+// The first warp stages a tile by bulk (TMA) copies: lane 0 arms the staging
+// barrier with the tile's byte count, then lane q < np copies halo piece q (a
+// contiguous run of 16-byte positions) and lane np the list block, if it fits
+// the stage (64-byte aligned, read rounded up to 16 bytes; the list and the
+// stage carry that slack).  The copies go out in parallel.
 __device__ __forceinline__ void issue_tile_bulk(const Bufs &b, const Tile &tl, const Piece *pc, int np, const uint4 *P,
-                                                uint4 *hpos, unsigned short *lst, unsigned long long *bar)
+                                                uint4 *hpos, unsigned short *lst, unsigned long long *bar, int lane)
 {
     const int Pt = tl.s1 - tl.s0;
     const unsigned lbytes = tl.kmax * Pt <= kListStage * kTileMax ? ((unsigned)(tl.kmax * Pt) * 2u + 15u) & ~15u : 0u;
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u + lbytes);
+    }
+    __syncwarp();
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u + lbytes);
-    for (int q = 0; q < np; ++q)
-        if (pc[q].n > 0) bulk_g2s(&hpos[pc[q].hoff], &P[pc[q].slot0], (unsigned)pc[q].n * 16u, bar);
-    if (lbytes) bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, bar);
+    if (lane < np) {
+        if (pc[lane].n > 0) bulk_g2s(&hpos[pc[lane].hoff], &P[pc[lane].slot0], (unsigned)pc[lane].n * 16u, bar);
+    } else if (lane == np && lbytes) {
+        bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, bar);
+    }
 }
 
 // HALF (FP32 only): the second kernel of a half-list step.  k_pairs_half has
@@ -735,7 +742,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 for (int p = threadIdx.x; p < Pt; p += blockDim.x) cp_async4(&s_nn[p], &b.nn[tl.s0 + p]);
             if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
             if (kBulk) {
-                if (threadIdx.x == 0 && !issued) issue_tile_bulk(b, tl, pc, np, P, hpos, lst, &s_mbar);
+                if (threadIdx.x < 32 && !issued) issue_tile_bulk(b, tl, pc, np, P, hpos, lst, &s_mbar, threadIdx.x);
             } else if (PREC == 1) stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
             else stage_halo<double>(pc, np, [&](int h, int j) {
                 cp_async8(&hx[h], &X[j]);
@@ -1023,9 +1030,9 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
         // With one particle per thread, the next tile's bulk copies go out as
         // soon as every thread is past its pair sums and arrive during phase 2:
         // each thread arrives on s_p1bar after phase 1 (the copying warp once its
-        // copies of the next tile's record are complete); only thread 0 waits
-        // for all of them, then issues.
-        int issued_next = 0;   // thread 0
+        // copies of the next tile's record are complete); only the first warp
+        // waits for all of them, then issues.
+        int issued_next = 0;   // the first warp (thread 0 publishes it)
         if (kBulk && Pt <= (int)blockDim.x) {
             PState ps;
             const long long i = tl.s0 + threadIdx.x;
@@ -1033,12 +1040,12 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             if (act) phase1(i, ps);
             cp_async_wait_all();   // the next tile's record (the copying warp)
             mbar_arrive(&s_p1bar);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < 32) {
                 if (!mbar_wait(&s_p1bar, p1phase)) err |= kErrTimeout;
                 else if (pref) {
                     const int npn = s_npb[buf ^ 1];
                     if (pcb[buf ^ 1][npn].hoff <= b.hcap) {
-                        issue_tile_bulk(b, tlb[buf ^ 1], pcb[buf ^ 1], npn, P, hpos, lst, &s_mbar);
+                        issue_tile_bulk(b, tlb[buf ^ 1], pcb[buf ^ 1], npn, P, hpos, lst, &s_mbar, threadIdx.x);
                         issued_next = 1;
                     }
                 }
