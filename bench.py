@@ -323,6 +323,31 @@ def timed_steps(md, torch, h, steps, stream):
     return e0.elapsed_time(e1), st0, st1, ck
 
 
+def forced_rebuilds(md, torch, h, stream, count=3):
+    """Full rebuilds (cell sort + Verlet list) of the current state through
+    md_build_neighbors, each timed with CUDA events, inside an NVTX range named
+    "forced rebuilds" that a profiler can select."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    try:
+        torch.cuda.nvtx.range_push("forced rebuilds")
+        pushed = True
+    except Exception:                      # no NVTX in this torch build: no range
+        pushed = False
+    ms = []
+    for _ in range(count):
+        e0.record(stream)
+        md.md_build_neighbors(h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    if pushed:
+        torch.cuda.nvtx.range_pop()
+    return {"mean": float(np.mean(ms)), "runs": [round(t, 4) for t in ms],
+            "note": "md_build_neighbors on the state after the timed steps: the whole cell sort + "
+                    "Verlet-list chain, CUDA events"}
+
+
 def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=None, steps=None, emit=True):
     # systems with bonds or angle triples add one kernel to each rebuild (the
     # slots of their partners)
@@ -338,6 +363,7 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=N
     md.md_step(h, steps)
     sect_ms, _ = md.md_get_timing(h)
     md.md_set_timing(h, False)
+    reb = forced_rebuilds(md, torch, h, stream)
     line = {"metric": f"{name} particle-steps/s", "value": n * steps / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -347,7 +373,7 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=N
             "gpu_launches": 2 * steps + 3 + chain_kernels * rb,
             "mean_list_len": st1["list_entries"] / n, "max_list_len": st1["max_list_len"],
             "max_cell_occupancy": st1["max_cell_occupancy"], "tiles": st1["n_tiles"],
-            "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck,
+            "max_halo": st1["max_halo"], "preparation": prep, "clocks": ck, "rebuild_ms": reb,
             "sections_ms_per_step": {"neigh": sect_ms[md.MD_SECT_NEIGH] / steps,
                                      "force_integrate": sect_ms[md.MD_SECT_FORCE] / steps,
                                      "other": sect_ms[md.MD_SECT_OTHER] / steps,
@@ -588,6 +614,9 @@ def main():
     md.md_step(h, args.steps)
     sect_ms, sect_n = md.md_get_timing(h)
     md.md_set_timing(h, False)
+    # full rebuilds of the steady-state system (cell sort + Verlet list), each
+    # timed with CUDA events, inside an NVTX range that a profiler can select
+    reb = forced_rebuilds(md, torch, h, stream)
 
     # ---- roofline of the dominant kernel (fused force + velocity Verlet)
     mean_nn = st1["list_entries"] / n
@@ -815,6 +844,7 @@ def main():
                                          "note": "second pass with per-launch events; the timed value "
                                                  "is the graph-launched pass"},
                 "mean_list_len": mean_nn,
+                "rebuild_ms": reb,
                 "clocks": ck,
                 "csrc_sha": digest}
         line.update(extras)
