@@ -86,7 +86,13 @@ typedef struct {
     int64_t n_bonds;                /* FENE bonds                               */
     const int32_t *bonds;           /* 2 * n_bonds particle indices, or NULL    */
     int32_t list_capacity;          /* neighbours per particle, rounded up to a
-                                       multiple of 32; 0 = automatic            */
+                                       multiple of 32; 0 = automatic: sized
+                                       from the mean density and grown until
+                                       the list fits by md_build_neighbors,
+                                       which the first md_step,
+                                       md_compute_forces or md_get_checkpoint
+                                       after md_set_state runs (synchronising
+                                       once)                                    */
     int32_t reserved0;
     double angle_K;                 /* bending constant of the angle term       */
     int64_t n_angles;               /* angle triples                            */

@@ -26,6 +26,7 @@ struct md_handle {
     bool auto_capacity = true;
     bool state_set = false;
     bool F_valid = false;
+    bool built = false;   // a growing list build (md_build_neighbors) ran since the last md_set_state
     long long N = 0, S = 0;
     int C = 0, nblk = 0, K = 0, nrows = 0;
     double *stage = nullptr;        // 6 * N doubles: in/out staging
@@ -693,7 +694,18 @@ md_status md_set_state(md_handle *h, const double *x, const double *v, void *str
     if (!cuda_ok(h, cudaGetLastError(), "set_state launch")) return MD_ERR_CUDA;
     h->state_set = true;
     h->F_valid = false;
+    h->built = false;
     return MD_OK;
+}
+
+// With an automatic list capacity, the first list of a new state is built by
+// md_build_neighbors, which grows the capacity until the list fits (the
+// capacity is first sized from the mean density, which an uneven system such
+// as a liquid/vapour slab exceeds).  One synchronisation per md_set_state.
+static md_status first_build(md_handle *h, void *stream)
+{
+    if (!h->auto_capacity || h->built) return MD_OK;
+    return md_build_neighbors(h, stream);
 }
 
 md_status md_get_state(md_handle *h, double *x, double *v, void *stream)
@@ -718,6 +730,8 @@ md_status md_get_checkpoint(md_handle *h, double *x, double *v, double *f, int64
     cudaStream_t st = (cudaStream_t)stream;
     // the force the next step starts from; evaluated now, as md_step would,
     // when none is stored
+    md_status s0 = first_build(h, stream);
+    if (s0 != MD_OK) return s0;
     if (!h->F_valid) {
         mdk::launch_rebuild_chain(h->b, st);
         mdk::launch_force(h->b, h->precision, mdk::kModeStore, false, st);
@@ -753,10 +767,11 @@ md_status md_set_checkpoint(md_handle *h, const double *x, const double *v, cons
     if (!cuda_ok(h, cudaMemcpyAsync(&h->b.ctl->step, &stp, sizeof(long long), cudaMemcpyHostToDevice, st),
                  "restore step"))
         return MD_ERR_CUDA;
-    // sort and build the list now, then put the stored force into the
-    // particles' new slots (the copy goes through the handle's staging buffer)
-    mdk::launch_set_rebuild(h->b, st);
-    mdk::launch_rebuild_chain(h->b, st);
+    // sort and build the list now (growing an automatic capacity as needed),
+    // then put the stored force into the particles' new slots (the copy goes
+    // through the handle's staging buffer)
+    s = md_build_neighbors(h, stream);
+    if (s != MD_OK) return s;
     double *fs = h->stage;
     if (!cuda_ok(h, cudaMemcpyAsync(fs, f, sizeof(double) * 3 * (size_t)h->N, cudaMemcpyDefault, st), "copy force in"))
         return MD_ERR_CUDA;
@@ -788,15 +803,21 @@ md_status md_build_neighbors(md_handle *h, void *stream)
         // the overflowing build still sorted the state; build again with the larger capacities
         mdk::launch_set_rebuild(h->b, st);
         mdk::launch_rebuild_chain(h->b, st);
-        return sync_and_check(h, st);
+        const md_status s2 = sync_and_check(h, st);
+        if (s2 == MD_OK) h->built = true;
+        return s2;
     }
-    return status_of(h, c.err);
+    const md_status s1 = status_of(h, c.err);
+    if (s1 == MD_OK) h->built = true;
+    return s1;
 }
 
 md_status md_compute_forces(md_handle *h, double *f_out, double *euw_out, void *stream)
 {
     if (!h) return MD_ERR_ARG;
     if (!h->state_set) return fail(h, MD_ERR_ARG, "md_compute_forces before md_set_state");
+    md_status s0 = first_build(h, stream);
+    if (s0 != MD_OK) return s0;
     cudaStream_t st = (cudaStream_t)stream;
     mdk::launch_rebuild_chain(h->b, st);
     h->F_valid = false;
@@ -901,6 +922,8 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
         return fail(h, MD_ERR_ARG, "md_step: bad arguments");
     if (!h->state_set) return fail(h, MD_ERR_ARG, "md_step before md_set_state");
     if (nsteps == 0) return MD_OK;
+    md_status s0 = first_build(h, stream);
+    if (s0 != MD_OK) return s0;
     if (!h->recover) return step_launch(h, nsteps, thermo_every, thermo_out, stream);
     // recovery: the step counter at the start of the call, then the call,
     // then (after a list or halo overflow) growth and the rest of the call

@@ -218,11 +218,12 @@ def sampled_check(md, h, n, sysm, x, idx, tol, bonded=False):
     return F
 
 
-def test_full_size_slab(md):
+def test_full_size_slab(md, report):
     """The liquid/vapour slab of the bench (N = 1,000,000, Lz = 4 Lx, liquid
     0.80 in the central quarter of z, vapour 0.02): forces of 2048 sampled
     particles, half of them from the vapour, and the neighbour rows of 512;
-    the first graph-launched step for the same particles."""
+    the first graph-launched step for the same particles; then the invariants
+    of a 300-step FP32 run (momentum, energy, reversibility)."""
     x, v, box = inputs.slab(1_000_000, rho_l=0.80, rho_v=0.02, T=0.8, seed=3, rmin=0.8)
     n = len(x)
     h = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT, precision=md.MD_FP32_FIXED)
@@ -250,6 +251,45 @@ def test_full_size_slab(md):
     Fo, _, _ = oracle.forces_sample(s, x, idx)
     err = np.linalg.norm(min_image_diff(x1[idx], x[idx] + DT * v[idx] + 0.5 * DT * DT * Fo, box), axis=1)
     assert np.all(err <= first_step_bound(Fo, 1e-5))
+    # the timed run itself: 300 graph-launched FP32 steps with (U, K, W) every
+    # step.  The fixed-point forces sum to exactly zero, so the total momentum
+    # moves only by the FP64 rounding of the kicks; 20 steps back with negated
+    # velocities return to the start.  The random placement (pairs down to
+    # 0.8 sigma) starts violent collisions, so the energy error is the time
+    # step's: the same time at dt / 2 cuts it about fourfold (second order).
+    def state(hh):
+        xo = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+        vo = torch.zeros_like(xo)
+        md.md_get_state(hh, xo, vo)
+        return xo.cpu().numpy().T.copy(), vo.cpu().numpy().T.copy()
+
+    th = np.zeros((300, 3))
+    md.md_step(h, 300, 1, th)
+    x300, v300 = state(h)
+    p1 = v300.sum(axis=0)
+    E = th[:, 0] + th[:, 1]
+    dE = float(np.max(np.abs(E - E[0])) / abs(E[0]))
+    st = md.md_get_stats(h)
+    h2 = md.md_create(n, box, rc_over_sigma=RC, skin=SKIN, dt=DT / 2, precision=md.MD_FP32_FIXED)
+    md.md_set_state(h2, dev(x), dev(v))
+    md.md_step(h2, 2)
+    th2 = np.zeros((602, 3))
+    md.md_step(h2, 602, 1, th2)
+    E2 = th2[:, 0] + th2[:, 1]
+    dE2 = float(np.max(np.abs(E2 - E2[0])) / abs(E2[0]))
+    h2.destroy()
+    report(f"slab N={n}, 300 FP32 steps: rebuilds {st['rebuilds']}, |sum p| {np.max(np.abs(p1)):.2e}, "
+           f"max |E - E0| / |E0| {dE:.2e} at dt {DT}, {dE2:.2e} at dt {DT / 2}")
+    assert np.max(np.abs(p1 - v.sum(axis=0))) < 1e-8
+    assert dE2 < dE / 2.5
+    md.md_step(h, 20)
+    x20, v20 = state(h)
+    md.md_set_state(h, dev(x20), dev(-v20))
+    md.md_step(h, 20)
+    xb, vb = state(h)
+    rev = float(np.max(np.abs(min_image_diff(xb, x300, box))))
+    report(f"slab N={n}: 20 steps forward and back, max |x - x0| {rev:.2e}")
+    assert rev < 1e-7
     h.destroy()
 
 
