@@ -77,6 +77,19 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// 1/a for a normal, positive a: the hardware reciprocal approximation refined
+// by two Newton-Raphson steps y <- y + y (1 - a y), each of which squares the
+// relative error, so the result is within about an ulp of 1/a.
+__device__ __forceinline__ double rcp_newton(double a)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    double e = __fma_rn(-a, y, 1.0);
+    y = __fma_rn(y, e, y);
+    e = __fma_rn(-a, y, 1.0);
+    return __fma_rn(y, e, y);
+}
+
 // Add round(f * 2^22) to the two-piece accumulator (valid for |f| < 2^21).
 __device__ __forceinline__ void fx_acc(float f, unsigned &hi, unsigned &lo)
 {
@@ -771,6 +784,27 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             err |= kErrTimeout;
             break;
         }
+        // FP64: the staged halo moved into the tile's periodic frame (each
+        // coordinate within half a box of the tile centre; the tile's own
+        // particles are halo entries too).  With at least 3 cells per axis and a
+        // tile at least 3 cells narrower than its row, every pair closer than a
+        // cell edge then has its minimum-image separation as the plain
+        // difference, so the neighbour loop takes no minimum image; any farther
+        // pair is beyond r_cut in every image.
+        const bool shifted = PREC == 0 && R.ncell[1] >= 3 && R.ncell[2] >= 3 && tl.x1 - tl.x0 <= R.ncell[0] - 3;
+        if (shifted) {
+            const double c0 = 0.5 * (tl.x0 + tl.x1) * R.L[0] / R.ncell[0];
+            const double c1 = (tl.cy + 0.5) * R.L[1] / R.ncell[1];
+            const double c2 = (tl.cz + 0.5) * R.L[2] / R.ncell[2];
+            const double g0 = 0.5 * R.L[0], g1 = 0.5 * R.L[1], g2 = 0.5 * R.L[2];
+            for (int h = threadIdx.x; h < pc[np].hoff; h += blockDim.x) {
+                const double t0 = hx[h] - c0, t1 = hy[h] - c1, t2 = hz[h] - c2;
+                if (t0 > g0) hx[h] -= R.L[0]; else if (t0 < -g0) hx[h] += R.L[0];
+                if (t1 > g1) hy[h] -= R.L[1]; else if (t1 < -g1) hy[h] += R.L[1];
+                if (t2 > g2) hz[h] -= R.L[2]; else if (t2 < -g2) hz[h] += R.L[2];
+            }
+            __syncthreads();
+        }
         // the last warp copies the next tile's record and pieces into the other
         // buffer while the tile is computed (not in the half-list pass, which
         // stages nothing and has little work per tile to hide the copy behind)
@@ -837,7 +871,12 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                     wf += fx_round(R.eps24_f * (a.sg.x + a.sg.y));
                 }
             } else {
-                const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
+                // in the tile's frame the particle's own coordinates come from its
+                // (shifted) halo entry: a particle that crossed the periodic
+                // boundary since the last build keeps its cell but wrapped
+                const int own = s_self + (int)(i - tl.s0);
+                const double xi0 = shifted ? hx[own] : X[i], xi1 = shifted ? hy[own] : X[b.S + i],
+                             xi2 = shifted ? hz[own] : X[2 * b.S + i];
                 const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
                 const double h0 = 0.5 * L0, h1 = 0.5 * L1, h2 = 0.5 * L2;
                 const double eps24 = 24.0 * R.eps, eps4 = 4.0 * R.eps, sig2 = R.sigma * R.sigma;
@@ -847,9 +886,11 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 for (int k = 0; k < n; ++k) {
                     const int h = lstaged ? nbs[k * Pt] : __ldg(nb + (long long)k * Pt);
                     double dx = xi0 - hx[h], dy = xi1 - hy[h], dz = xi2 - hz[h];
-                    dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
-                    dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
-                    dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
+                    if (!shifted) {
+                        dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
+                        dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
+                        dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
+                    }
                     const double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 < rc2 + band) {
                         bool in = r2 < rc2 - band;
@@ -869,7 +910,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                                 wi += 0.5 * fs * r2;
                             }
                         } else if (in) {
-                            const double ir2 = 1.0 / r2;
+                            const double ir2 = rcp_newton(r2);
                             const double s2 = sig2 * ir2;
                             const double s6 = s2 * s2 * s2;
                             const double fs = eps24 * s6 * (2.0 * s6 - 1.0) * ir2;
