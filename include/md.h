@@ -49,7 +49,8 @@ typedef enum {
     MD_ERR_BOND_BROKEN = -5,    /* a FENE bond reached r >= R0               */
     MD_ERR_FIXED_OVERFLOW = -6, /* a pair force exceeded the fixed-point range */
     MD_ERR_TIMEOUT = -7,        /* a bounded device wait gave up             */
-    MD_ERR_BOX_TOO_SMALL = -8   /* a box edge is shorter than 2 (r_cut + r_skin) */
+    MD_ERR_BOX_TOO_SMALL = -8,  /* a box edge is shorter than 2 (r_cut + r_skin) */
+    MD_ERR_BOUNDS = -9          /* a device-side bounds check failed (checked build) */
 } md_status;
 
 /* md_params.potential.  MD_SOFT is the cosine push-off A (1 + cos(pi r / r_cut))
@@ -121,6 +122,8 @@ typedef struct {
     int32_t halo_capacity;      /* shared-memory halo capacity (particles)    */
     int32_t tile_size;          /* particles per tile the tiler aims at        */
     int64_t recoveries;         /* md_step overflows recovered (md_set_recovery) */
+    int64_t bad_index;          /* checked build: the index that failed at bad_site */
+    int32_t bad_site;           /* checked build: the first failing bounds check, else 0 */
 } md_stats;
 
 /* Create a handle for the replicas described by p (Sec. 2.1: cells of edge
@@ -218,6 +221,49 @@ md_status md_set_recovery(md_handle *h, int32_t enable);
  * counterpart.  MD_ERR_ARG for polls outside 1..65536.  Asynchronous. */
 md_status md_check_wait_timeout(md_handle *h, int32_t polls, void *stream);
 
+/* Build flags of the loaded library: MD_BUILD_CHECKED for the checked build
+ * (libmd_gb300_checked.so, compiled with -DMD_CHECKED), else 0.  In the
+ * checked build every kernel checks the indices that the data layout keeps
+ * in range by construction -- cell ids, bucket and destination slots,
+ * particle ids, tile and halo-piece indices, candidate ranges, list entries
+ * against the staged halo, the slots behind halo entries, bond and angle
+ * partners.  A failed check latches MD_ERR_BOUNDS, with the first failing
+ * site and index (md_stats.bad_site / bad_index, and the message of
+ * md_last_error), and the access is replaced by a harmless one: nothing
+ * traps, the context stays usable, and md_set_state clears the error.  It is
+ * the device-side stand-in for a memory checker; the default build compiles
+ * every check away.  No passage of the paper: a debugging aid of this
+ * library. */
+#define MD_BUILD_CHECKED 1
+int md_build_flags(void);
+
+/* Sites of the checked build's bounds checks (md_stats.bad_site). */
+typedef enum {
+    MD_SITE_BIN_CELL = 1,      /* binning: a particle's cell within its replica's cells */
+    MD_SITE_SCATTER = 2,       /* counting sort: a bucket slot within its cell's slots  */
+    MD_SITE_REORDER = 3,       /* re-sort: the particle id and the destination slot     */
+    MD_SITE_TOPOLOGY = 4,      /* bond and angle partner ids                           */
+    MD_SITE_TILE_WRITE = 5,    /* tiling: a tile's index within the tile table          */
+    MD_SITE_PIECES = 6,        /* tiling: halo pieces within kMaxPieces and the slots   */
+    MD_SITE_LIST_RANGE = 7,    /* list build: a candidate range within the halo         */
+    MD_SITE_LIST_SELF = 8,     /* list build: the tile's own entries within the halo    */
+    MD_SITE_FORCE_HALO = 9,    /* force kernels: a list entry within the staged halo    */
+    MD_SITE_FORCE_OWN = 10,    /* force kernels: a particle's own halo entry            */
+    MD_SITE_FORCE_SLOT = 11,   /* force kernels: the slot behind a halo entry           */
+    MD_SITE_BOND_SLOT = 12,    /* force kernel: a bond or angle partner's slot          */
+    MD_SITE_ADJ = 13           /* reverse pass: a list entry, particle id or slot       */
+} md_check_site;
+
+/* Self-test of the checked build's bounds checks: makes the checks of `site`
+ * (an md_check_site) fail on purpose on their next evaluations, with the
+ * index they see (which is in range), so that each site's failure path -- the
+ * latch, the report, the harmless replacement access -- runs without a bad
+ * access.
+ * The next synchronising call that runs that site returns MD_ERR_BOUNDS;
+ * md_set_state disarms it.  site 0 disarms it too.  MD_ERR_ARG in the default
+ * build or for a site out of range.  Synchronises `stream`. */
+md_status md_check_bounds_selftest(md_handle *h, int32_t site, void *stream);
+
 /* Differentiable run (reverse-mode differentiation of the velocity-Verlet map
  * of Fig. 1; the paper itself has no gradients).  Advance nsteps NVE steps from
  * the current state, keeping (x, v) every ckpt_every steps in device memory the
@@ -242,7 +288,10 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
  * sigma moving with sigma (pairs crossing r_cut contribute jump terms that are
  * not included).  Recomputes each segment from its checkpoint; Hessian-vector
  * products and all adjoint sums in FP64.  Leaves the handle at the final state
- * of the recorded run (step counter and stats reset).  Synchronises `stream`. */
+ * of the recorded run (step counter and stats reset).  A device error latched
+ * during the pass is returned as soon as it is seen (checked once per
+ * segment), with the handle at a checkpoint's state: md_set_state before
+ * further use.  Synchronises `stream`. */
 md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, const double *dL_deuw,
                       double *dL_deps, double *dL_dsigma, void *stream);
 

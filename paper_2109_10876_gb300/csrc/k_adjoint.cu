@@ -35,6 +35,12 @@ __device__ __forceinline__ int adj_halo_slot(const Piece *pc, int np, int h)
     return pc[q].slot0 + (h - pc[q].hoff);
 }
 
+// bounds check of the checked build (md_ok): v within [0, lim), else 0
+__device__ __forceinline__ long long adj_checked(Ctl *ctl, long long v, long long lim)
+{
+    return md_ok(ctl, v >= 0 && v < lim, kSiteAdjHalo, v) ? v : 0;
+}
+
 // Last block: per-replica sums of the 4 per-tile partials, added into
 // acc[4 * r + k] with weight `scale`.  Each warp takes every fourth replica:
 // lane-strided sums over its tiles, then a shuffle tree (a fixed order, so
@@ -90,7 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
             hy[h] = X[b.S + j];
             hz[h] = X[2 * b.S + j];
             if (MODE == 0) {
-                const int id = (int)P[j].w;
+                const int id = (int)adj_checked(b.ctl, (int)P[j].w, b.N);
                 hw[3 * h + 0] = w[id];
                 hw[3 * h + 1] = w[b.N + id];
                 hw[3 * h + 2] = w[2 * b.N + id];
@@ -104,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
         const double band = 1e-12 * rc2;
         double p0 = 0.0, p1 = 0.0, p2 = 0.0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
-            const int id = (int)P[i].w;
+            const int id = (int)adj_checked(b.ctl, (int)P[i].w, b.N);
             const int n = min(b.nn[i], b.K);
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
             const double xi0 = X[i], xi1 = X[b.S + i], xi2 = X[2 * b.S + i];
@@ -113,14 +119,16 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
             double acc3[3] = {0, 0, 0}, F[3] = {0, 0, 0}, Fs[3] = {0, 0, 0};
             double u = 0.0, wv = 0.0, ws = 0.0;
             for (int k = 0; k < n; ++k) {
-                const int h = __ldg(nb + (long long)k * Pt);
+                const int h = (int)adj_checked(b.ctl, __ldg(nb + (long long)k * Pt), pc[np].hoff);
                 double dx = xi0 - hx[h], dy = xi1 - hy[h], dz = xi2 - hz[h];
                 dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
                 dy = dy > h1 ? dy - L1 : (dy < -h1 ? dy + L1 : dy);
                 dz = dz > h2 ? dz - L2 : (dz < -h2 ? dz + L2 : dz);
                 const double r2 = dx * dx + dy * dy + dz * dz;
                 if (!(r2 < rc2 + band)) continue;
-                if (!(r2 < rc2 - band) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < rc2)) continue;
+                if (!(r2 < rc2 - band) &&
+                    !(adj_r2_exact(X, b.S, i, adj_checked(b.ctl, adj_halo_slot(pc, np, h), b.S), R.L) < rc2))
+                    continue;
                 // one FP64 division per pair (the FP64 divide is a long sequence)
                 const double ir2 = 1.0 / r2;
                 const double s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
@@ -265,7 +273,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
         double p0 = 0.0, p1 = 0.0;
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
             const uint4 pi = P[i];
-            const int id = (int)pi.w;
+            const int id = (int)adj_checked(b.ctl, (int)pi.w, b.N);
             const int n = min(b.nn[i], b.K);
             const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
             const double wi0 = w[id], wi1 = w[b.N + id], wi2 = w[2 * b.N + id];
@@ -279,7 +287,8 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
             for (int k0 = 0; k0 < n; k0 += 8) {
                 int hh[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) hh[u] = k0 + u < n ? (int)__ldg(nb + (long long)(k0 + u) * Pt) : -1;
+                for (int u = 0; u < 8; ++u)
+                    hh[u] = k0 + u < n ? (int)adj_checked(b.ctl, __ldg(nb + (long long)(k0 + u) * Pt), pc[np].hoff) : -1;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int h = hh[u];
@@ -290,7 +299,9 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
                     const float dz = (float)(int)(pi.z - pj.z) * qs2;
                     const float r2 = dx * dx + dy * dy + dz * dz;
                     if (!(r2 < hi)) continue;
-                    if (!(r2 < lo) && !(adj_r2_exact(X, b.S, i, adj_halo_slot(pc, np, h), R.L) < R.rc2)) continue;
+                    if (!(r2 < lo) &&
+                        !(adj_r2_exact(X, b.S, i, adj_checked(b.ctl, adj_halo_slot(pc, np, h), b.S), R.L) < R.rc2))
+                        continue;
                     const float ir2 = rcp_approx_f(r2);
                     const float s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
                     const float e24 = eps24 * ir2;

@@ -73,6 +73,9 @@ __global__ void k_reset_ctl(Ctl *ctl)
     ctl->step = 0;
     ctl->rebuilds = 0;
     ctl->list_entries = 0;
+    ctl->bad_site = 0;
+    ctl->plant = 0;
+    ctl->bad_index = 0;
 }
 
 // Caller layout (3, N) -> slot layout; initial slot order = caller order.
@@ -232,7 +235,10 @@ __global__ void k_bin(Bufs b)
                 int cx, cy, cz;
                 cell_coords(p, R, cx, cy, cz);
                 c = R.cell_off + (cz * R.ncell[1] + cy) * R.ncell[0] + cx;
-                b.cellid[s] = c;
+                if (md_ok(b.ctl, c >= R.cell_off && c < R.cell_off + R.ncells && c < b.C, kSiteBinCell, s))
+                    b.cellid[s] = c;
+                else
+                    c = -1;
             }
         }
         const unsigned peers = __match_any_sync(full, c);
@@ -338,7 +344,11 @@ __global__ void k_scatter(Bufs b)
         int base = 0;
         if (c >= 0 && lane == leader) base = atomicAdd(&b.cell_end[c], __popc(peers));
         base = __shfl_sync(full, base, leader);
-        if (c >= 0) b.bucket[base + __popc(peers & ((1u << lane) - 1u))] = (int)s;
+        if (c >= 0) {
+            const int dst = base + __popc(peers & ((1u << lane) - 1u));
+            const int lim = c + 1 < b.C ? b.cell_start[c + 1] : (int)b.S;
+            if (md_ok(b.ctl, dst >= b.cell_start[c] && dst < lim, kSiteScatter, dst)) b.bucket[dst] = (int)s;
+        }
     }
 }
 
@@ -353,6 +363,7 @@ __device__ __forceinline__ unsigned long long order_key(uint4 p)
 
 __device__ __forceinline__ void reorder_move(const Bufs &b, int cur, int nxt, int c, int s, int dst, uint4 p)
 {
+    if (!md_ok(b.ctl, (int)p.w >= 0 && (long long)p.w < b.N && dst >= 0 && dst < b.S, kSiteReorder, dst)) return;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         b.x[nxt][k * b.S + dst] = b.x[cur][k * b.S + s];
@@ -379,7 +390,8 @@ __global__ void k_reorder(Bufs b)
         if (lane == 0) b.cell_count[c] = 0;   // histogram is clean for the next build
         if (n <= 32) {
             const bool act = lane < n;
-            const int s = act ? b.bucket[start + lane] : 0;
+            int s = act ? b.bucket[start + lane] : 0;
+            if (act && !md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
             const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
             const unsigned long long key = act ? order_key(p) : ~0ULL;
             int rank = 0;
@@ -389,10 +401,15 @@ __global__ void k_reorder(Bufs b)
         }
         for (int m = lane; m < n; m += 32) {
             int s = b.bucket[start + m];
+            if (!md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
             uint4 p = pin[s];
             const unsigned long long key = order_key(p);
             int rank = 0;
-            for (int q = 0; q < n; ++q) rank += (order_key(pin[b.bucket[start + q]]) < key);
+            for (int q = 0; q < n; ++q) {
+                int sq = b.bucket[start + q];
+                if (!md_ok(b.ctl, sq >= 0 && sq < b.S, kSiteReorder, sq)) sq = 0;
+                rank += (order_key(pin[sq]) < key);
+            }
             reorder_move(b, cur, nxt, c, s, start + rank, p);
         }
     }
@@ -407,10 +424,16 @@ __global__ void k_topology_slots(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < b.n_bond_ent) b.bond_pslot[q] = b.slot_of_id[b.bond_partner[q]];
+    auto id_ok = [&](int id) { return md_ok(b.ctl, id >= 0 && id < b.N, kSiteTopology, id); };
+    if (q < b.n_bond_ent) {
+        const int id = b.bond_partner[q];
+        b.bond_pslot[q] = id_ok(id) ? b.slot_of_id[id] : 0;
+    }
     if (q < b.n_ang_ent) {
         const int4 e = b.ang_ent[q];
-        b.ang_slot[q] = make_int4(b.slot_of_id[e.x], b.slot_of_id[e.y], b.slot_of_id[e.z], e.w);
+        const bool ok = id_ok(e.x) & id_ok(e.y) & id_ok(e.z);
+        b.ang_slot[q] = ok ? make_int4(b.slot_of_id[e.x], b.slot_of_id[e.y], b.slot_of_id[e.z], e.w)
+                           : make_int4(0, 0, 0, e.w);
     }
 }
 
@@ -480,7 +503,7 @@ __device__ int walk_row(const Bufs &b, int g, Tile *out, int *colsum, int *own)
                 H = Hn;
                 ++x1;
             }
-            if (out) {
+            if (out && md_ok(b.ctl, (out - b.tiles) + nt < b.C, kSiteTileWrite, (out - b.tiles) + nt)) {
                 const int base = R.cell_off + (cz * ny + cy) * nx;
                 Tile t;
                 t.rep = r; t.cy = cy; t.cz = cz; t.x0 = x0; t.x1 = x1;
@@ -590,11 +613,14 @@ __global__ void __launch_bounds__(32 * kTileWarps) k_tile_pieces(Bufs b)
         for (int q = 0; q < npc; ++q) {
             Piece pq;
             pq.row = lane; pq.xa = ra[q]; pq.xb = rb[q]; pq.slot0 = s0[q]; pq.hoff = h; pq.n = cnt[q];
-            out[pbase + q] = pq;
+            // a piece's slots lie within the slots (its bulk copy reads them)
+            if (md_ok(b.ctl, pbase + q < kMaxPieces && s0[q] >= 0 && cnt[q] >= 0 && s0[q] + cnt[q] <= b.S,
+                      kSitePieces, (long long)t * (kMaxPieces + 1) + pbase + q))
+                out[pbase + q] = pq;
             h += cnt[q];
         }
         const int np = __shfl_sync(0xffffffffu, pinc, 31), H = __shfl_sync(0xffffffffu, hinc, 31);
-        if (lane == 0) {
+        if (lane == 0 && md_ok(b.ctl, np <= kMaxPieces, kSitePieces, (long long)t * (kMaxPieces + 1) + np)) {
             Piece last;
             last.row = nrow; last.xa = last.xb = 0; last.slot0 = 0; last.hoff = H; last.n = 0;
             out[np] = last;
@@ -702,6 +728,7 @@ __device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, con
     rh1 = rh0 + (j1 - j0);
     rj0 = j0;
     if (rh0 < pc[qq].hoff || rh1 > pc[qq].hoff + pc[qq].n) { err |= kErrList; rh1 = rh0; return; }
+    if (!md_ok(b.ctl, rh0 >= 0 && rh1 <= pc[np].hoff, kSiteListRange, rh1)) { rh0 = rh1 = 0; return; }
     if constexpr (REL) {
         // Rows are sorted along x (cells in order, members by x), and so are
         // the group's own particles: candidates farther along x than the
@@ -761,6 +788,9 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
     // stage rows of this tile (0: no stage, every list goes to global memory)
     const int cap = Pt <= kTileMax ? min((kListStage * kTileMax) / max(Pt, 1), b.K) : 0;
     unsigned short *dummy = lst + kListStage * kTileMax;     // one slot per lane
+    // the tile's own particles are halo entries [hfirst, hfirst + Pt) (same
+    // decision in every thread)
+    if (!md_ok(b.ctl, hfirst >= 0 && hfirst + Pt <= pc[np].hoff, kSiteListSelf, hfirst)) return;
     for (int c0 = warp * 32; c0 < Pt; c0 += nwarp * 32) {
         const int pp = c0 + lane;
         const bool valid = pp < Pt;

@@ -370,6 +370,20 @@ __device__ __forceinline__ int halo_slot(const Piece *pc, int np, int h)
     return pc[q].slot0 + (h - pc[q].hoff);
 }
 
+// bounds checks of the checked build (md_ok): a list entry within the
+// staged halo of hsize entries (else entry 0), a slot within the S slots
+// (else slot i, the particle's own)
+__device__ __forceinline__ int checked_entry(Ctl *ctl, int h, int hsize, int site)
+{
+    return md_ok(ctl, (unsigned)h < (unsigned)hsize, site, h) ? h : 0;
+}
+
+__device__ __forceinline__ long long checked_slot(Ctl *ctl, long long j, long long S, long long i,
+                                                  int site = kSiteForceSlot)
+{
+    return md_ok(ctl, j >= 0 && j < S, site, j) ? j : i;
+}
+
 // All lengths in fixed-point units u of the x axis: r2 and d in u, the force
 // scalar fs in force / u (constants pre-scaled), so fs * d is the force.
 template <bool ENERGY>
@@ -434,7 +448,7 @@ __device__ __forceinline__ void sep_u(uint4 a, uint4 c, float ry, float rz, floa
 template <bool ENERGY, bool CUBIC, bool LSMEM>
 __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos, const unsigned short *nb, int Pt,
                                              int n, int npad, uint4 pi, const double *X, long long S, long long i,
-                                             const Piece *pc, int np, Acc32 &a, int &err)
+                                             const Piece *pc, int np, Acc32 &a, int &err, Ctl *ctl, int hsize)
 {
     const float ry = R.ry, rz = R.rz;
     const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
@@ -444,7 +458,9 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
     for (int k0 = 0; k0 < npad; k0 += kU) {
         int hh[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) hh[u] = LSMEM ? nb[(k0 + u) * Pt] : __ldg(nb + (long long)(k0 + u) * Pt);
+        for (int u = 0; u < kU; ++u)
+            hh[u] = checked_entry(ctl, LSMEM ? nb[(k0 + u) * Pt] : __ldg(nb + (long long)(k0 + u) * Pt), hsize,
+                                  kSiteForceHalo);
 #pragma unroll
         for (int u = 0; u < kU; u += 2) {
             const uint4 q0 = lds128(hpos + hh[u]), q1 = lds128(hpos + hh[u + 1]);
@@ -473,10 +489,10 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
         // pairs within rounding of r_cut: membership decided in FP64 from the
         // master positions, as in the FP64 reference
         for (int k = 0; k < n; ++k) {
-            const int h = nb[(long long)k * Pt];
+            const int h = checked_entry(ctl, nb[(long long)k * Pt], hsize, kSiteForceHalo);
             float dx, dy, dz, r2;
             sep_u<CUBIC>(pi, hpos[h], ry, rz, dx, dy, dz, r2);
-            if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, halo_slot(pc, np, h), R.L) < R.rc2)
+            if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, checked_slot(ctl, halo_slot(pc, np, h), S, i), R.L) < R.rc2)
                 pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, a);
         }
     }
@@ -565,7 +581,8 @@ __device__ __forceinline__ void pair32x2_half(float2 dx, float2 dy, float2 dz, f
 template <bool ENERGY, bool CUBIC>
 __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 *hpos, const unsigned short *nb, int Pt,
                                                   int n, int npad, uint4 pi, const double *X, long long S, long long i,
-                                                  const Piece *pc, int np, Acc32 &a, int &err, long long *Fq)
+                                                  const Piece *pc, int np, Acc32 &a, int &err, long long *Fq,
+                                                  Ctl *ctl, int hsize)
 {
     const float ry = R.ry, rz = R.rz;
     const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
@@ -575,10 +592,12 @@ __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 
     for (int k0 = 0; k0 < npad; k0 += kU) {
         int hh[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) hh[u] = nb[(k0 + u) * Pt];
+        for (int u = 0; u < kU; ++u) hh[u] = checked_entry(ctl, nb[(k0 + u) * Pt], hsize, kSiteForceHalo);
 #pragma unroll
         for (int u = 0; u < kU; u += 2) {
-            const uint4 q0 = hpos[hh[u]], q1 = hpos[hh[u + 1]];
+            uint4 q0 = hpos[hh[u]], q1 = hpos[hh[u + 1]];
+            q0.w = (unsigned)checked_slot(ctl, (int)q0.w, S, i);   // where the reactions go
+            q1.w = (unsigned)checked_slot(ctl, (int)q1.w, S, i);
             float2 dx = make_float2((float)(int)(pi.x - q0.x), (float)(int)(pi.x - q1.x));
             float2 dy = make_float2((float)(int)(pi.y - q0.y), (float)(int)(pi.y - q1.y));
             float2 dz = make_float2((float)(int)(pi.z - q0.z), (float)(int)(pi.z - q1.z));
@@ -600,8 +619,9 @@ __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 
     }
     if (nband) {
         for (int k = 0; k < n; ++k) {
-            const int h = nb[k * Pt];
-            const uint4 q = hpos[h];
+            const int h = checked_entry(ctl, nb[k * Pt], hsize, kSiteForceHalo);
+            uint4 q = hpos[h];
+            q.w = (unsigned)checked_slot(ctl, (int)q.w, S, i);
             float dx, dy, dz, r2;
             sep_u<CUBIC>(pi, q, ry, rz, dx, dy, dz, r2);
             if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, (long long)q.w, R.L) < R.rc2) {
@@ -829,7 +849,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 prefetch_l1(&X[i]); prefetch_l1(&X[b.S + i]); prefetch_l1(&X[2 * b.S + i]);
                 prefetch_l1(&b.xref[i]);
             }
-            ps.pi = (PREC == 1 && !HALF) ? hpos[s_self + (int)(i - tl.s0)] : P[i];
+            ps.pi = (PREC == 1 && !HALF) ? hpos[checked_entry(b.ctl, s_self + (int)(i - tl.s0), pc[np].hoff, kSiteForceOwn)]
+                                         : P[i];
             const uint4 pi = ps.pi;
             const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
             const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
@@ -853,11 +874,11 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
                 if (lstaged) {
                     const unsigned short *nbs = lst + (i - tl.s0);
-                    if (R.cubic) neighbours32<ENERGY, true, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
-                    else neighbours32<ENERGY, false, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
+                    if (R.cubic) neighbours32<ENERGY, true, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.ctl, pc[np].hoff);
+                    else neighbours32<ENERGY, false, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.ctl, pc[np].hoff);
                 } else {
-                    if (R.cubic) neighbours32<ENERGY, true, false>(R, hpos, nb, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
-                    else neighbours32<ENERGY, false, false>(R, hpos, nb, Pt, n, npad, pi, X, b.S, i, pc, np, a, err);
+                    if (R.cubic) neighbours32<ENERGY, true, false>(R, hpos, nb, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.ctl, pc[np].hoff);
+                    else neighbours32<ENERGY, false, false>(R, hpos, nb, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.ctl, pc[np].hoff);
                 }
                 const unsigned hs[3] = {a.hx, a.hy, a.hz}, ls[3] = {a.lx, a.ly, a.lz};
 #pragma unroll
@@ -874,7 +895,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 // in the tile's frame the particle's own coordinates come from its
                 // (shifted) halo entry: a particle that crossed the periodic
                 // boundary since the last build keeps its cell but wrapped
-                const int own = s_self + (int)(i - tl.s0);
+                const int own = checked_entry(b.ctl, s_self + (int)(i - tl.s0), pc[np].hoff, kSiteForceOwn);
                 const double xi0 = shifted ? hx[own] : X[i], xi1 = shifted ? hy[own] : X[b.S + i],
                              xi2 = shifted ? hz[own] : X[2 * b.S + i];
                 const double L0 = R.L[0], L1 = R.L[1], L2 = R.L[2];
@@ -884,7 +905,8 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 const double band = 1e-12 * rc2;
                 const unsigned short *nbs = lst + (i - tl.s0);
                 for (int k = 0; k < n; ++k) {
-                    const int h = lstaged ? nbs[k * Pt] : __ldg(nb + (long long)k * Pt);
+                    const int h = checked_entry(b.ctl, lstaged ? nbs[k * Pt] : __ldg(nb + (long long)k * Pt),
+                                                pc[np].hoff, kSiteForceHalo);
                     double dx = xi0 - hx[h], dy = xi1 - hy[h], dz = xi2 - hz[h];
                     if (!shifted) {
                         dx = dx > h0 ? dx - L0 : (dx < -h0 ? dx + L0 : dx);
@@ -894,7 +916,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                     const double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 < rc2 + band) {
                         bool in = r2 < rc2 - band;
-                        if (!in) in = r2_exact(X, b.S, i, halo_slot(pc, np, h), R.L) < rc2;
+                        if (!in) in = r2_exact(X, b.S, i, checked_slot(b.ctl, halo_slot(pc, np, h), b.S, i), R.L) < rc2;
                         if (in && R.soft) {
                             // cosine push-off A (1 + cos(pi r / r_cut)), A = eps:
                             // -dV/dr = (pi A / r_cut) sin(pi r / r_cut), none at r = 0
@@ -937,7 +959,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
             if (b.has_bonds) {
                 const int id = (int)pi.w;
                 for (int q = b.bond_off[id]; q < b.bond_off[id + 1]; ++q) {
-                    const int sj = b.bond_pslot[q];
+                    const int sj = (int)checked_slot(b.ctl, b.bond_pslot[q], b.S, i, kSiteBondSlot);
                     if (PREC == 1) {
                         const uint4 pj = P[sj];
                         const float dx = (float)(int)(pi.x - pj.x) * R.qs[0];
@@ -980,7 +1002,9 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 const int id = (int)pi.w;
                 for (int q = b.ang_off[id]; q < b.ang_off[id + 1]; ++q) {
                     const int4 e = b.ang_slot[q];      // slots of (a, b, c), role in .w
-                    const int sa = e.x, sb = e.y, sc = e.z;
+                    const int sa = (int)checked_slot(b.ctl, e.x, b.S, i, kSiteBondSlot),
+                              sb = (int)checked_slot(b.ctl, e.y, b.S, i, kSiteBondSlot),
+                              sc = (int)checked_slot(b.ctl, e.z, b.S, i, kSiteBondSlot);
                     if (PREC == 1) {
                         const uint4 pa = P[sa], pb = P[sb], pcc = P[sc];
                         const float b1[3] = {(float)(int)(pb.x - pa.x) * R.qs[0], (float)(int)(pb.y - pa.y) * R.qs[1],
@@ -1193,15 +1217,17 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
         stage_halo<uint4>(pc, np, [&](int h, int j) { hpos[h].w = (unsigned)j; });
         __syncthreads();
         for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
-            const uint4 pi = hpos[s_self + (int)(i - tl.s0)];
+            const uint4 pi = hpos[checked_entry(b.ctl, s_self + (int)(i - tl.s0), pc[np].hoff, kSiteForceOwn)];
             const int n = min(own_staged ? s_nn[i - tl.s0] : b.nn[i], b.K);
             const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
             // a list block too long for the stage is read from global memory
             // through the same [row][particle] layout
             const unsigned short *nbs = lstaged ? lst + (i - tl.s0) : b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
             Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
-            if (R.cubic) neighbours32_half<ENERGY, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq);
-            else neighbours32_half<ENERGY, false>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq);
+            if (R.cubic) neighbours32_half<ENERGY, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq, b.ctl,
+                                                  pc[np].hoff);
+            else neighbours32_half<ENERGY, false>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq, b.ctl,
+                                                   pc[np].hoff);
             const unsigned hs[3] = {a.hx, a.hy, a.hz}, ls[3] = {a.lx, a.ly, a.lz};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {

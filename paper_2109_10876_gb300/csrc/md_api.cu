@@ -103,10 +103,47 @@ double lj_fmag(double r, double eps, double sig)
 
 long long round_up(long long a, long long m) { return (a + m - 1) / m * m; }
 
-// Map latched device error bits to a status.
-md_status status_of(md_handle *h, int bits)
+static_assert(mdk::kSiteBinCell == MD_SITE_BIN_CELL && mdk::kSiteScatter == MD_SITE_SCATTER &&
+                  mdk::kSiteReorder == MD_SITE_REORDER && mdk::kSiteTopology == MD_SITE_TOPOLOGY &&
+                  mdk::kSiteTileWrite == MD_SITE_TILE_WRITE && mdk::kSitePieces == MD_SITE_PIECES &&
+                  mdk::kSiteListRange == MD_SITE_LIST_RANGE && mdk::kSiteListSelf == MD_SITE_LIST_SELF &&
+                  mdk::kSiteForceHalo == MD_SITE_FORCE_HALO && mdk::kSiteForceOwn == MD_SITE_FORCE_OWN &&
+                  mdk::kSiteForceSlot == MD_SITE_FORCE_SLOT && mdk::kSiteBondSlot == MD_SITE_BOND_SLOT &&
+                  mdk::kSiteAdjHalo == MD_SITE_ADJ && mdk::kSiteCount == MD_SITE_ADJ + 1,
+              "check sites of md.h and of the kernels agree");
+
+const char *site_name(int site)
 {
+    static const char *names[mdk::kSiteCount] = {
+        "none",
+        "cell of a particle (binning)",
+        "bucket slot (scatter)",
+        "particle id or destination slot (re-sort)",
+        "bond or angle partner id (topology)",
+        "tile index (tiling)",
+        "halo piece (tiling)",
+        "candidate range in the halo (list build)",
+        "own halo entries (list build)",
+        "list entry in the halo (force)",
+        "own halo entry (force)",
+        "slot of a halo entry (force)",
+        "bond or angle partner slot (force)",
+        "list entry, id or slot (reverse pass)",
+    };
+    return site > 0 && site < mdk::kSiteCount ? names[site] : "unknown";
+}
+
+// Map latched device error bits to a status.
+md_status status_of(md_handle *h, const Ctl &c)
+{
+    const int bits = c.err;
     if (!bits) return MD_OK;
+    if (bits & mdk::kErrBounds) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "device bounds check failed: site %d (%s), index %lld", c.bad_site,
+                      site_name(c.bad_site), (long long)c.bad_index);
+        return fail(h, MD_ERR_BOUNDS, msg);
+    }
     if (bits & mdk::kErrList) return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour list capacity exceeded");
     if (bits & mdk::kErrBond) return fail(h, MD_ERR_BOND_BROKEN, "FENE bond reached r >= R0");
     if (bits & mdk::kErrFixed) return fail(h, MD_ERR_FIXED_OVERFLOW, "pair force outside the fixed-point range");
@@ -210,7 +247,7 @@ md_status sync_and_check(md_handle *h, cudaStream_t st)
     Ctl c;
     md_status s = read_ctl(h, &c);
     if (s != MD_OK) return s;
-    return status_of(h, c.err);
+    return status_of(h, c);
 }
 
 // Capture f(stream) into graph g after deps; tail gets the captured sink nodes.
@@ -807,7 +844,7 @@ md_status md_build_neighbors(md_handle *h, void *stream)
         if (s2 == MD_OK) h->built = true;
         return s2;
     }
-    const md_status s1 = status_of(h, c.err);
+    const md_status s1 = status_of(h, c);
     if (s1 == MD_OK) h->built = true;
     return s1;
 }
@@ -938,7 +975,7 @@ md_status md_step(md_handle *h, int32_t nsteps, int32_t thermo_every, double *th
     for (int attempt = 0;; ++attempt) {
         if (!cuda_ok(h, cudaStreamSynchronize(st), "stream synchronize")) return MD_ERR_CUDA;
         if ((s = read_ctl(h, &c)) != MD_OK) return s;
-        if (c.err != mdk::kErrList || attempt == 4) return status_of(h, c.err);
+        if (c.err != mdk::kErrList || attempt == 4) return status_of(h, c);
         if ((s = grow_after_overflow(h, c)) != MD_OK) return s;
         h->recoveries += 1;
         const long long done = c.step - step0;   // drifts completed before the failing rebuild
@@ -967,6 +1004,24 @@ md_status md_check_wait_timeout(md_handle *h, int32_t polls, void *stream)
     if (polls < 1 || polls > 65536) return fail(h, MD_ERR_ARG, "md_check_wait_timeout: polls outside 1..65536");
     mdk::launch_wait_selftest(h->b, polls, (cudaStream_t)stream);
     return cuda_ok(h, cudaGetLastError(), "self-test launch") ? MD_OK : MD_ERR_CUDA;
+}
+
+int md_build_flags(void)
+{
+    return mdk::kChecked ? MD_BUILD_CHECKED : 0;
+}
+
+md_status md_check_bounds_selftest(md_handle *h, int32_t site, void *stream)
+{
+    if (!h) return MD_ERR_ARG;
+    if (!mdk::kChecked) return fail(h, MD_ERR_ARG, "md_check_bounds_selftest: not a checked build (MD_CHECKED)");
+    if (site < 0 || site >= mdk::kSiteCount) return fail(h, MD_ERR_ARG, "md_check_bounds_selftest: site out of range");
+    const int v = site;
+    return cuda_ok(h, cudaMemcpyAsync(&h->b.ctl->plant, &v, sizeof(int), cudaMemcpyHostToDevice, (cudaStream_t)stream),
+                   "arm bounds self-test") &&
+                   cuda_ok(h, cudaStreamSynchronize((cudaStream_t)stream), "arm bounds self-test")
+               ? MD_OK
+               : MD_ERR_CUDA;
 }
 
 md_status md_set_recovery(md_handle *h, int32_t enable)
@@ -1030,7 +1085,9 @@ md_status md_get_stats(md_handle *h, md_stats *out)
     out->halo_capacity = h->b.hcap;
     out->tile_size = h->b.tile_max;
     out->recoveries = h->recoveries;
-    return status_of(h, c.err);
+    out->bad_site = c.bad_site;
+    out->bad_index = c.bad_index;
+    return status_of(h, c);
 }
 
 md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *euw_out, void *stream)
@@ -1138,6 +1195,10 @@ md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, co
         for (int c = nseg - 1; c >= 0; --c) {
             const int t0 = c * k, t1 = std::min(T, (c + 1) * k);
             const double *ck = h->ad_ck + (long long)c * 2 * n3;
+            // an error latched by the reverse pass so far is reported before
+            // md_set_state clears the error word for the segment's re-run
+            s = sync_and_check(h, st);
+            if (s != MD_OK) return s;
             s = md_set_state(h, ck, ck + n3, st);
             if (s != MD_OK) return s;
             if (!cuda_ok(h, cudaMemcpyAsync(h->ad_seg, ck, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st), "copy"))

@@ -43,6 +43,27 @@ enum : int {
     kErrBond = 4,
     kErrFixed = 8,
     kErrTimeout = 16,
+    kErrBounds = 32,     // a device-side bounds check failed (checked build only)
+};
+
+// Sites of the device-side bounds checks of the checked build: each names an
+// index that the data layout keeps in range by construction.
+enum CheckSite : int {
+    kSiteNone = 0,
+    kSiteBinCell = 1,      // k_bin: a particle's cell within its replica's cells
+    kSiteScatter = 2,      // k_scatter: a bucket slot within its cell's slots
+    kSiteReorder = 3,      // k_reorder: the particle id and the destination slot
+    kSiteTopology = 4,     // k_topology_slots: bond and angle partner ids
+    kSiteTileWrite = 5,    // tiling: a tile's index within the tile table
+    kSitePieces = 6,       // k_tile_pieces: a tile's piece count within kMaxPieces
+    kSiteListRange = 7,    // list build: a candidate range within the staged halo
+    kSiteListSelf = 8,     // list build: a particle's own halo entry within the halo
+    kSiteForceHalo = 9,    // force kernels: a list entry within the staged halo
+    kSiteForceOwn = 10,    // force kernels: a particle's own halo entry within the halo
+    kSiteForceSlot = 11,   // force kernels: the slot behind a halo entry within the slots
+    kSiteBondSlot = 12,    // force kernel: a bond or angle partner's slot within the slots
+    kSiteAdjHalo = 13,     // reverse pass: a list entry within the staged halo, an id or slot in range
+    kSiteCount = 14,
 };
 
 // Per-replica constants (device copy written once at create time).
@@ -96,7 +117,37 @@ struct Ctl {
     long long rec;           // energy records written by this graph-launched md_step
     long long rebuilds;
     long long list_entries;
+    int bad_site;            // checked build: the first failing bounds check (CheckSite), else 0
+    int plant;               // checked build: a site whose next checks are made to fail (self-test), else 0
+    long long bad_index;     // checked build: the index that failed at bad_site
 };
+
+#ifdef MD_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// A device-side bounds check.  In the default build it is `true` and
+// compiles away.  Built with -DMD_CHECKED it returns `ok`; on a failure it
+// latches kErrBounds, with the first failing site and index in the control
+// block, and the caller replaces the access by a harmless one: nothing traps,
+// so the context stays usable and the host reports MD_ERR_BOUNDS.  A site
+// named by Ctl::plant fails on purpose (with an index in range), so that a
+// test can exercise every site's failure path without a bad access.
+__device__ __forceinline__ bool md_ok(Ctl *ctl, bool ok, int site, long long idx)
+{
+    if constexpr (!kChecked) {
+        return true;
+    } else {
+        ok = ok && ctl->plant != site;
+        if (!ok) {
+            if (atomicCAS(&ctl->bad_site, 0, site) == 0) ctl->bad_index = idx;
+            atomicOr(&ctl->err, kErrBounds);
+        }
+        return ok;
+    }
+}
 
 // A tile: row (cy, cz) of replica rep, cells [x0, x1) along x, particles in
 // slots [s0, s1), halo of hsize particles.

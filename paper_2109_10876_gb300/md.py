@@ -8,7 +8,9 @@ component-major layout.  Streams are torch.cuda.Stream objects, raw
 cudaStream_t integers, or None for the current torch stream.
 
 Importing this module loads the library and raises if it is missing: there
-is no fallback implementation.
+is no fallback implementation.  With MD_GB300_CHECKED=1 in the environment it
+loads the checked build lib/libmd_gb300_checked.so instead (device-side
+bounds checks, md_build_flags() & MD_BUILD_CHECKED).
 """
 import ctypes as C
 import os
@@ -16,7 +18,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libmd_gb300.so")
+CHECKED = os.environ.get("MD_GB300_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "lib", "libmd_gb300_checked.so" if CHECKED else "libmd_gb300.so")
 
 MD_OK = 0
 MD_ERR_ARG = -1
@@ -27,9 +30,17 @@ MD_ERR_BOND_BROKEN = -5
 MD_ERR_FIXED_OVERFLOW = -6
 MD_ERR_TIMEOUT = -7
 MD_ERR_BOX_TOO_SMALL = -8
+MD_ERR_BOUNDS = -9
 STATUS_NAMES = {0: "MD_OK", -1: "MD_ERR_ARG", -2: "MD_ERR_CUDA", -3: "MD_ERR_LIST_OVERFLOW",
                 -4: "MD_ERR_NONFINITE", -5: "MD_ERR_BOND_BROKEN", -6: "MD_ERR_FIXED_OVERFLOW",
-                -7: "MD_ERR_TIMEOUT", -8: "MD_ERR_BOX_TOO_SMALL"}
+                -7: "MD_ERR_TIMEOUT", -8: "MD_ERR_BOX_TOO_SMALL", -9: "MD_ERR_BOUNDS"}
+MD_BUILD_CHECKED = 1
+# md_check_site
+MD_SITES = {1: "MD_SITE_BIN_CELL", 2: "MD_SITE_SCATTER", 3: "MD_SITE_REORDER", 4: "MD_SITE_TOPOLOGY",
+            5: "MD_SITE_TILE_WRITE", 6: "MD_SITE_PIECES", 7: "MD_SITE_LIST_RANGE", 8: "MD_SITE_LIST_SELF",
+            9: "MD_SITE_FORCE_HALO", 10: "MD_SITE_FORCE_OWN", 11: "MD_SITE_FORCE_SLOT", 12: "MD_SITE_BOND_SLOT",
+            13: "MD_SITE_ADJ"}
+globals().update({v: k for k, v in MD_SITES.items()})
 MD_LJ, MD_WCA, MD_SOFT = 0, 1, 2
 MD_SECT_NEIGH, MD_SECT_FORCE, MD_SECT_OTHER, MD_NSECT = 0, 1, 2, 3
 MD_FP64, MD_FP32_FIXED = 0, 1
@@ -80,6 +91,8 @@ class md_stats(C.Structure):
         ("halo_capacity", C.c_int32),
         ("tile_size", C.c_int32),
         ("recoveries", C.c_int64),
+        ("bad_index", C.c_int64),
+        ("bad_site", C.c_int32),
     ]
 
 
@@ -121,6 +134,10 @@ _lib.md_set_recovery.restype = C.c_int
 _lib.md_set_recovery.argtypes = [_H, C.c_int32]
 _lib.md_check_wait_timeout.restype = C.c_int
 _lib.md_check_wait_timeout.argtypes = [_H, C.c_int32, _vp]
+_lib.md_build_flags.restype = C.c_int
+_lib.md_build_flags.argtypes = []
+_lib.md_check_bounds_selftest.restype = C.c_int
+_lib.md_check_bounds_selftest.argtypes = [_H, C.c_int32, _vp]
 _lib.md_autotune.restype = C.c_int
 _lib.md_autotune.argtypes = [_H, C.c_int32, C.POINTER(C.c_int32), _vp]
 _lib.md_set_tile_size.restype = C.c_int
@@ -300,6 +317,14 @@ def md_check_wait_timeout(h, polls=1000, stream=None):
     return _check(h.ptr, _lib.md_check_wait_timeout(h.ptr, int(polls), _stream(stream)))
 
 
+def md_build_flags():
+    return int(_lib.md_build_flags())
+
+
+def md_check_bounds_selftest(h, site, stream=None):
+    return _check(h.ptr, _lib.md_check_bounds_selftest(h.ptr, int(site), _stream(stream)))
+
+
 def md_export_pairs(h, pairs_out, capacity, stream=None):
     n = C.c_int64(0)
     _check(h.ptr, _lib.md_export_pairs(h.ptr, _ptr(pairs_out), int(capacity), C.byref(n), _stream(stream)))
@@ -326,10 +351,13 @@ def md_sync(h, stream=None):
     return _check(h.ptr, _lib.md_sync(h.ptr, _stream(stream)))
 
 
-def md_get_stats(h):
+def md_get_stats(h, check=True):
+    """md_get_stats as a dict; check=False returns the figures even when the
+    call reports a latched device error (error_word, bad_site, bad_index)."""
     s = md_stats()
     st = _lib.md_get_stats(h.ptr, C.byref(s))
-    _check(h.ptr, st)
+    if check:
+        _check(h.ptr, st)
     return {f: (list(getattr(s, f)) if f == "ncell" else getattr(s, f)) for f, _ in md_stats._fields_}
 
 

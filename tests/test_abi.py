@@ -37,6 +37,18 @@ def test_every_declared_symbol_is_exported(md):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 
 
+def test_checked_build_exports_the_same_symbols(md):
+    """The checked build (-DMD_CHECKED) exports every declared symbol, and
+    md_build_flags (no device call) tells the two builds apart."""
+    from paper_2109_10876_gb300 import build
+    assert os.path.exists(build.LIB_CHECKED)
+    checked = C.CDLL(build.LIB_CHECKED)
+    for n in declared_functions():
+        assert hasattr(checked, n), f"{n} declared in include/ but not exported by the checked build"
+    assert checked.md_build_flags() == md.MD_BUILD_CHECKED
+    assert C.CDLL(md.LIB_PATH).md_build_flags() == 0
+
+
 def _c_layout(struct, fields, tmp_path):
     """sizeof and offsetof of `struct` from the C compiler reading include/md.h."""
     inc = os.path.join(ROOT, "include")
