@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(kBlock) k_adj(Bufs b, const double *w, double 
                 if (!(r2 < rc2 - band) &&
                     !(adj_r2_exact(X, b.S, i, adj_checked(b.ctl, adj_halo_slot(pc, np, h), b.S), R.L) < rc2))
                     continue;
-                // one FP64 division per pair (the FP64 divide is a long sequence)
-                const double ir2 = 1.0 / r2;
+                // 1/r^2 by the reciprocal approximation and two Newton steps (the
+                // IEEE divide is a long sequence on the narrow FP64 pipe)
+                const double ir2 = rcp_newton(r2);
                 const double s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
                 const double e24 = eps24 * ir2;
                 const double g = e24 * (2.0 * s12 - s6);
@@ -236,19 +237,133 @@ __global__ void k_adj_wslots(Bufs b, const double *w)
 // r_cut), pair terms and per-particle sums in FP32, w staged as FP32 (hi, lo)
 // pairs so that w_i - w_j keeps about 48 bits.  The adjoint state itself
 // (lx, lv) and the parameter projections stay FP64.
-__global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, double *out, double scale, double *acc)
+// Staged like the force kernel: the first warp copies the tile's halo
+// positions and list block by bulk (TMA) copies onto an mbarrier (a bounded
+// wait); the fourth word of each staged position is then replaced by its slot,
+// where the entry's w pieces are read.  The pair loop takes two neighbours at
+// a time with packed FP32 instructions and no branches: entries beyond r_cut
+// (and the padding) are masked, and their w is not read; entries within FP32
+// rounding of r_cut are settled afterwards in FP64.
+
+// The pair terms of one neighbour (scalar) or two (packed), added into the
+// per-particle sums: acc += g dw + g' (d.dw) d, F += g d, Fs += dg/dsigma d,
+// with g = 24 eps (2 s^12 - s^6) / r^2.
+struct HvpSums {
+    float2 ax, ay, az, fx, fy, fz, sx, sy, sz;
+};
+
+// a - b for two lanes (the negation is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+__device__ __forceinline__ void hvp_pair2(float2 dx, float2 dy, float2 dz, float2 ir2, float4 wa0, float2 wb0,
+                                          float4 wa1, float2 wb1, const float4 &wai, const float2 &wbi, float sig2,
+                                          float eps24, float isig, HvpSums &a)
+{
+    const float2 s2 = __fmul2_rn(make_float2(sig2, sig2), ir2);
+    const float2 s6 = __fmul2_rn(__fmul2_rn(s2, s2), s2);
+    const float2 s12 = __fmul2_rn(s6, s6);
+    const float2 e24 = __fmul2_rn(make_float2(eps24, eps24), ir2);
+    const float2 g = __fmul2_rn(e24, __ffma2_rn(make_float2(2.0f, 2.0f), s12, make_float2(-s6.x, -s6.y)));
+    const float2 gpr = __fmul2_rn(__fmul2_rn(e24, ir2),
+                                  __ffma2_rn(make_float2(8.0f, 8.0f), s6, __fmul2_rn(make_float2(-28.0f, -28.0f), s12)));
+    const float2 dgds = __fmul2_rn(__fmul2_rn(e24, make_float2(isig, isig)),
+                                   __ffma2_rn(make_float2(24.0f, 24.0f), s12, __fmul2_rn(make_float2(-6.0f, -6.0f), s6)));
+    // w_i - w_j from the (hi, lo) pieces
+    const float2 dwx = __fadd2_rn(sub2(make_float2(wai.x, wai.x), make_float2(wa0.x, wa1.x)),
+                                  sub2(make_float2(wai.w, wai.w), make_float2(wa0.w, wa1.w)));
+    const float2 dwy = __fadd2_rn(sub2(make_float2(wai.y, wai.y), make_float2(wa0.y, wa1.y)),
+                                  sub2(make_float2(wbi.x, wbi.x), make_float2(wb0.x, wb1.x)));
+    const float2 dwz = __fadd2_rn(sub2(make_float2(wai.z, wai.z), make_float2(wa0.z, wa1.z)),
+                                  sub2(make_float2(wbi.y, wbi.y), make_float2(wb0.y, wb1.y)));
+    const float2 ddw = __ffma2_rn(dz, dwz, __ffma2_rn(dy, dwy, __fmul2_rn(dx, dwx)));
+    const float2 gd = __fmul2_rn(gpr, ddw);
+    a.ax = __fadd2_rn(a.ax, __ffma2_rn(g, dwx, __fmul2_rn(gd, dx)));
+    a.ay = __fadd2_rn(a.ay, __ffma2_rn(g, dwy, __fmul2_rn(gd, dy)));
+    a.az = __fadd2_rn(a.az, __ffma2_rn(g, dwz, __fmul2_rn(gd, dz)));
+    a.fx = __ffma2_rn(g, dx, a.fx);
+    a.fy = __ffma2_rn(g, dy, a.fy);
+    a.fz = __ffma2_rn(g, dz, a.fz);
+    a.sx = __ffma2_rn(dgds, dx, a.sx);
+    a.sy = __ffma2_rn(dgds, dy, a.sy);
+    a.sz = __ffma2_rn(dgds, dz, a.sz);
+}
+
+// One particle's HVP sums from its list (entry k at nb[k Pt]: the staged list
+// block when LSMEM, else the list in global memory).
+template <bool LSMEM>
+__device__ __forceinline__ void hvp_particle(const Bufs &b, const Replica &R, const uint4 *hpos, int H,
+                                             const unsigned short *nb, int Pt, int n, int npad, uint4 pi,
+                                             long long i, const float4 &wai, const float2 &wbi, HvpSums &a)
+{
+    const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
+    const float lo = R.rc2_lo, hi = R.rc2_hi;
+    const float eps24 = 24.0f * (float)R.eps, sig2 = (float)(R.sigma * R.sigma), isig = (float)(1.0 / R.sigma);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 z2 = make_float2(0.f, 0.f);
+    int nband = 0;
+    for (int k0 = 0; k0 < npad; k0 += 4) {
+        int hh[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            hh[u] = (int)adj_checked(b.ctl, LSMEM ? nb[(k0 + u) * Pt] : __ldg(nb + (long long)(k0 + u) * Pt), H);
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+            const uint4 q0 = lds128(hpos + hh[u]), q1 = lds128(hpos + hh[u + 1]);
+            const float2 dx = __fmul2_rn(make_float2((float)(int)(pi.x - q0.x), (float)(int)(pi.x - q1.x)),
+                                         make_float2(qs0, qs0));
+            const float2 dy = __fmul2_rn(make_float2((float)(int)(pi.y - q0.y), (float)(int)(pi.y - q1.y)),
+                                         make_float2(qs1, qs1));
+            const float2 dz = __fmul2_rn(make_float2((float)(int)(pi.z - q0.z), (float)(int)(pi.z - q1.z)),
+                                         make_float2(qs2, qs2));
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            // padding entries are the particle itself (r^2 = 0)
+            const bool in0 = (r2.x < lo) & (r2.x > 0.0f), in1 = (r2.y < lo) & (r2.y > 0.0f);
+            nband += ((r2.x < hi) & !(r2.x < lo)) + ((r2.y < hi) & !(r2.y < lo));
+            float2 ir2 = make_float2(rcp_approx_f(r2.x), rcp_approx_f(r2.y));
+            ir2.x = in0 ? ir2.x : 0.0f;
+            ir2.y = in1 ? ir2.y : 0.0f;
+            const long long j0 = adj_checked(b.ctl, (long long)q0.w, b.S), j1 = adj_checked(b.ctl, (long long)q1.w, b.S);
+            const float4 wa0 = in0 ? __ldg(b.adj_wa + j0) : z4, wa1 = in1 ? __ldg(b.adj_wa + j1) : z4;
+            const float2 wb0 = in0 ? __ldg(b.adj_wb + j0) : z2, wb1 = in1 ? __ldg(b.adj_wb + j1) : z2;
+            hvp_pair2(dx, dy, dz, ir2, wa0, wb0, wa1, wb1, wai, wbi, sig2, eps24, isig, a);
+        }
+    }
+    if (nband) {
+        // pairs within rounding of r_cut: membership decided in FP64 from the
+        // master positions; each as one lane of a packed pair (the other masked)
+        for (int k = 0; k < n; ++k) {
+            const int h = (int)adj_checked(b.ctl, LSMEM ? nb[k * Pt] : __ldg(nb + (long long)k * Pt), H);
+            const uint4 q = lds128(hpos + h);
+            const float dx = (float)(int)(pi.x - q.x) * qs0, dy = (float)(int)(pi.y - q.y) * qs1,
+                        dz = (float)(int)(pi.z - q.z) * qs2;
+            const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, dx * dx));
+            const long long j = adj_checked(b.ctl, (long long)q.w, b.S);
+            if (!(r2 < lo) && r2 < hi && adj_r2_exact(b.x[b.ctl->cur], b.S, i, j, R.L) < R.rc2)
+                hvp_pair2(make_float2(dx, 0.f), make_float2(dy, 0.f), make_float2(dz, 0.f),
+                          make_float2(rcp_approx_f(r2), 0.f), __ldg(b.adj_wa + j), __ldg(b.adj_wb + j), z4, z2, wai,
+                          wbi, sig2, eps24, isig, a);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, 4) k_adj_hvp32(Bufs b, const double *w, double *out, double scale,
+                                                         double *acc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Piece pc[kMaxPieces + 1];
     __shared__ Tile tl;
-    __shared__ int s_tile, s_np;
-    __shared__ double sm4[kBlock / 32][4];
+    __shared__ int s_tile, s_np, s_self;
+    __shared__ double sm4[kBlock / 32][2];
+    __shared__ __align__(8) unsigned long long s_mbar;   // completion of a tile's bulk copies
     __shared__ bool last;
     if (block_uniform(b.ctl->err != 0)) return;
     const int cur = b.ctl->cur;
-    const double *X = b.x[cur];
     const uint4 *P = b.pos[cur];
     uint4 *hpos = reinterpret_cast<uint4 *>(smem_raw);
+    unsigned short *lst = reinterpret_cast<unsigned short *>(smem_raw + (size_t)b.hcap * sizeof(uint4));
+    if (threadIdx.x == 0) mbar_init(&s_mbar, 1);
+    unsigned phase = 0;
+    int err = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(&b.ctl->tile_next, 1u);
         __syncthreads();
@@ -259,74 +374,47 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
         const Replica &R = b.rep[tl.rep];
         const int np = s_np;
         const int Pt = tl.s1 - tl.s0;
-        // positions only (the halo's w is read by slot from the slot-ordered
-        // table, which stays in L1 for the tile); the fourth word becomes the slot
-        stage_halo<uint4>(pc, np, [&](int h, int j) { cp_async16(&hpos[h], &P[j]); });
-        cp_async_wait_all();
-        __syncthreads();
-        stage_halo<uint4>(pc, np, [&](int h, int j) { hpos[h].w = (unsigned)j; });
-        __syncthreads();
-        const float qs0 = R.qs[0], qs1 = R.qs[1], qs2 = R.qs[2];
-        const float lo = R.rc2_lo, hi = R.rc2_hi;
-        const float eps24 = 24.0f * (float)R.eps, sig2 = (float)(R.sigma * R.sigma), isig = (float)(1.0 / R.sigma);
-        const double ieps = 1.0 / R.eps;
+        const int H = pc[np].hoff;
         double p0 = 0.0, p1 = 0.0;
-        for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
-            const uint4 pi = P[i];
-            const int id = (int)adj_checked(b.ctl, (int)pi.w, b.N);
-            const int n = min(b.nn[i], b.K);
-            const unsigned short *nb = b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
-            const double wi0 = w[id], wi1 = w[b.N + id], wi2 = w[2 * b.N + id];
-            const float4 wai = b.adj_wa[i];
-            const float2 wbi = b.adj_wb[i];
-            const float ah0 = wai.x, ah1 = wai.y, ah2 = wai.z;
-            const float al0 = wai.w, al1 = wbi.x, al2 = wbi.y;
-            float acc3[3] = {0.f, 0.f, 0.f}, F[3] = {0.f, 0.f, 0.f}, Fs[3] = {0.f, 0.f, 0.f};
-            // eight list entries in flight at a time (the list is read from
-            // global memory; its latency, not the arithmetic, sets the pace)
-            for (int k0 = 0; k0 < n; k0 += 8) {
-                int hh[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    hh[u] = k0 + u < n ? (int)adj_checked(b.ctl, __ldg(nb + (long long)(k0 + u) * Pt), pc[np].hoff) : -1;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int h = hh[u];
-                    if (h < 0) continue;
-                    const uint4 pj = hpos[h];
-                    const float dx = (float)(int)(pi.x - pj.x) * qs0;
-                    const float dy = (float)(int)(pi.y - pj.y) * qs1;
-                    const float dz = (float)(int)(pi.z - pj.z) * qs2;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (!(r2 < hi)) continue;
-                    if (!(r2 < lo) &&
-                        !(adj_r2_exact(X, b.S, i, adj_checked(b.ctl, adj_halo_slot(pc, np, h), b.S), R.L) < R.rc2))
-                        continue;
-                    const float ir2 = rcp_approx_f(r2);
-                    const float s2 = sig2 * ir2, s6 = s2 * s2 * s2, s12 = s6 * s6;
-                    const float e24 = eps24 * ir2;
-                    const float g = e24 * (2.0f * s12 - s6);
-                    const float gpr = e24 * ir2 * (8.0f * s6 - 28.0f * s12);
-                    const float dgds = e24 * isig * (24.0f * s12 - 6.0f * s6);
-                    const float4 wa = __ldg(b.adj_wa + pj.w);
-                    const float2 wb = __ldg(b.adj_wb + pj.w);
-                    const float dw0 = (ah0 - wa.x) + (al0 - wa.w);
-                    const float dw1 = (ah1 - wa.y) + (al1 - wb.x);
-                    const float dw2 = (ah2 - wa.z) + (al2 - wb.y);
-                    const float ddw = dx * dw0 + dy * dw1 + dz * dw2;
-                    const float gd = gpr * ddw;
-                    acc3[0] += g * dw0 + gd * dx;
-                    acc3[1] += g * dw1 + gd * dy;
-                    acc3[2] += g * dw2 + gd * dz;
-                    F[0] += g * dx; F[1] += g * dy; F[2] += g * dz;
-                    Fs[0] += dgds * dx; Fs[1] += dgds * dy; Fs[2] += dgds * dz;
-                }
+        if (H <= b.hcap) {   // block-uniform; the list build rejects larger halos first
+            if (threadIdx.x == 0) s_self = tile_self_offset(R, tl, pc, np);
+            if (threadIdx.x < 32) issue_tile_bulk(b, tl, pc, np, P, hpos, lst, &s_mbar, threadIdx.x);
+            const bool late = !mbar_wait(&s_mbar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(late)) {   // a bulk copy never completed: stop, report
+                err |= kErrTimeout;
+                break;
             }
-            for (int q = 0; q < 3; ++q) out[q * b.N + id] = (double)acc3[q];
-            p0 += (wi0 * F[0] + wi1 * F[1] + wi2 * F[2]) * ieps;
-            p1 += wi0 * Fs[0] + wi1 * Fs[1] + wi2 * Fs[2];
+            // the fourth word of each staged position becomes its slot
+            stage_halo<uint4>(pc, np, [&](int h, int j) { hpos[h].w = (unsigned)j; });
+            __syncthreads();
+            const bool lstaged = tl.kmax * Pt <= kListStage * kTileMax;
+            const double ieps = 1.0 / R.eps;
+            for (long long i = tl.s0 + threadIdx.x; i < tl.s1; i += blockDim.x) {
+                const int p = (int)(i - tl.s0);
+                const uint4 pi = lds128(hpos + adj_checked(b.ctl, s_self + p, H));
+                const int id = (int)adj_checked(b.ctl, (int)P[i].w, b.N);
+                const int n = min(b.nn[i], b.K);
+                const int npad = min(((n + kPad - 1) / kPad) * kPad, b.K);
+                const float4 wai = b.adj_wa[i];
+                const float2 wbi = b.adj_wb[i];
+                HvpSums a;
+                a.ax = a.ay = a.az = a.fx = a.fy = a.fz = a.sx = a.sy = a.sz = make_float2(0.f, 0.f);
+                if (lstaged) hvp_particle<true>(b, R, hpos, H, lst + p, Pt, n, npad, pi, i, wai, wbi, a);
+                else
+                    hvp_particle<false>(b, R, hpos, H, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, p), Pt, n, npad, pi, i,
+                                        wai, wbi, a);
+                out[id] = (double)(a.ax.x + a.ax.y);
+                out[b.N + id] = (double)(a.ay.x + a.ay.y);
+                out[2 * b.N + id] = (double)(a.az.x + a.az.y);
+                const double wi0 = w[id], wi1 = w[b.N + id], wi2 = w[2 * b.N + id];
+                p0 += (wi0 * (a.fx.x + a.fx.y) + wi1 * (a.fy.x + a.fy.y) + wi2 * (a.fz.x + a.fz.y)) * ieps;
+                p1 += wi0 * (a.sx.x + a.sx.y) + wi1 * (a.sy.x + a.sy.y) + wi2 * (a.sz.x + a.sz.y);
+            }
+        } else {
+            err |= kErrList;
         }
-        // per-tile partials in a fixed order
+        // per-tile partials in a fixed order (zero for a rejected tile)
         for (int o = 16; o > 0; o >>= 1) {
             p0 += __shfl_down_sync(0xffffffffu, p0, o);
             p1 += __shfl_down_sync(0xffffffffu, p1, o);
@@ -343,6 +431,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_hvp32(Bufs b, const double *w, d
         }
         __syncthreads();
     }
+    if (err) atomicOr(&b.ctl->err, err);
     if (threadIdx.x == 0) {
         __threadfence();
         last = (atomicAdd(&b.ctl->done_force, 1u) == gridDim.x - 1);
@@ -406,7 +495,7 @@ void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, d
                     cudaStream_t st)
 {
     if (precision == 1) {
-        const size_t smem32 = (size_t)b.hcap * sizeof(uint4);
+        const size_t smem32 = (size_t)b.hcap * sizeof(uint4) + (size_t)kListStage * kTileMax * sizeof(unsigned short);
         static int grid32 = 0;
         static size_t gs32 = 0;
         if (grid32 == 0 || gs32 != smem32) { grid32 = adj_grid((const void *)k_adj_hvp32, smem32); gs32 = smem32; }

@@ -59,35 +59,12 @@ __device__ __forceinline__ void fx_acc2x2(float2 a, float2 c, unsigned &hi, unsi
     lo += __float_as_uint(t2.x) + __float_as_uint(t2.y);
 }
 
-// One 16-byte shared-memory load of a staged halo position (the compiler
-// would otherwise split it when the fourth word is not used).
-__device__ __forceinline__ uint4 lds128(const uint4 *p)
-{
-    uint4 q;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w) : "r"(a));
-    return q;
-}
-
 // Reciprocal by the hardware approximation (a pure function of its input).
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// 1/a for a normal, positive a: the hardware reciprocal approximation refined
-// by two Newton-Raphson steps y <- y + y (1 - a y), each of which squares the
-// relative error, so the result is within about an ulp of 1/a.
-__device__ __forceinline__ double rcp_newton(double a)
-{
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-    double e = __fma_rn(-a, y, 1.0);
-    y = __fma_rn(y, e, y);
-    e = __fma_rn(-a, y, 1.0);
-    return __fma_rn(y, e, y);
 }
 
 // Add round(f * 2^22) to the two-piece accumulator (valid for |f| < 2^21).
@@ -663,30 +640,8 @@ __device__ __forceinline__ void angle_term(const Real b1[3], const Real b2[3], R
 // a4 + a5: forces on every particle of a tile from its Verlet list, with
 // the neighbour positions read from the tile's halo in shared memory, then
 // the velocity-Verlet update of that particle.  Persistent blocks take tiles
-// from a work counter.
-// The first warp stages a tile by bulk (TMA) copies: lane 0 arms the staging
-// barrier with the tile's byte count, then lane q < np copies halo piece q (a
-// contiguous run of 16-byte positions) and lane np the list block, if it fits
-// the stage (64-byte aligned, read rounded up to 16 bytes; the list and the
-// stage carry that slack).  The copies go out in parallel.
-__device__ __forceinline__ void issue_tile_bulk(const Bufs &b, const Tile &tl, const Piece *pc, int np, const uint4 *P,
-                                                uint4 *hpos, unsigned short *lst, unsigned long long *bar, int lane)
-{
-    const int Pt = tl.s1 - tl.s0;
-    const unsigned lbytes = tl.kmax * Pt <= kListStage * kTileMax ? ((unsigned)(tl.kmax * Pt) * 2u + 15u) & ~15u : 0u;
-    if (lane == 0) {
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u + lbytes);
-    }
-    __syncwarp();
-    fence_proxy_async_smem();
-    if (lane < np) {
-        if (pc[lane].n > 0) bulk_g2s(&hpos[pc[lane].hoff], &P[pc[lane].slot0], (unsigned)pc[lane].n * 16u, bar);
-    } else if (lane == np && lbytes) {
-        bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, bar);
-    }
-}
-
+// from a work counter; the first warp stages each FP32 tile by bulk (TMA)
+// copies (issue_tile_bulk).
 // HALF (FP32 only): the second kernel of a half-list step.  k_pairs_half has
 // left each particle's total pair force in the fixed-point sums Fq; this pass
 // takes it from there (and clears it) instead of walking a list, then does

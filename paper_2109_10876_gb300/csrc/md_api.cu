@@ -550,13 +550,25 @@ md_status md_create(const md_params *p, md_handle **out)
     }
     if (K > 65535) { delete h; return MD_ERR_ARG; }
 
-    // halo capacity of the tile kernels: 3 x 3 rows of a full tile of
-    // kTileMax particles plus two cells' worth at the mean occupancy (the
-    // tiler keeps every halo within it; md_build_neighbors grows it when one
-    // cell's halo alone does not fit)
-    double occ = 0;
-    for (auto &R : h->reps) occ = std::fmax(occ, R.ncells ? (double)R.n / R.ncells : 0.0);
-    int hcap = (int)round_up((long long)(9.0 * (mdk::kTileMax + 2.0 * occ + 16.0)), 128);
+    // halo capacity of the tile kernels, the largest over the replicas of: the
+    // halo rows (3 x 3, fewer on axes of one or two cells), each holding a full
+    // tile of kTileMax particles plus two cells at the mean occupancy, or the
+    // whole row where that is less, with a margin; and never more than the
+    // replica's particles, since a halo holds each of its cells once.  The
+    // tiler keeps every halo within it (md_build_neighbors grows it when one
+    // cell's halo alone does not fit), and a smaller capacity leaves room for
+    // more blocks of the tile kernels per SM.
+    double hneed = 0;
+    for (auto &R : h->reps) {
+        if (!R.ncells) continue;
+        const double occ = (double)R.n / R.ncells;
+        int ly, cy, lz, cz;
+        mdk::axis_offsets(R.ncell[1], ly, cy);
+        mdk::axis_offsets(R.ncell[2], lz, cz);
+        const double row = std::fmin(R.ncell[0] * occ, mdk::kTileMax + 2.0 * occ) + 16.0;
+        hneed = std::fmax(hneed, std::fmin((double)R.n, cy * cz * row));
+    }
+    int hcap = (int)round_up((long long)std::ceil(hneed), 128);
     hcap = std::min(std::max(hcap, 1024), 8192);
 
     Bufs &b = h->b;

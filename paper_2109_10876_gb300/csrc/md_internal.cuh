@@ -423,6 +423,53 @@ __device__ __forceinline__ int tile_self_offset(const Replica &R, const Tile &tl
     return pc[q].hoff + (tl.s0 - pc[q].slot0);
 }
 
+// 1/a for a normal, positive a: the hardware reciprocal approximation refined
+// by two Newton-Raphson steps y <- y + y (1 - a y), each of which squares the
+// relative error, so the result is within about an ulp of 1/a.
+__device__ __forceinline__ double rcp_newton(double a)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+    double e = __fma_rn(-a, y, 1.0);
+    y = __fma_rn(y, e, y);
+    e = __fma_rn(-a, y, 1.0);
+    return __fma_rn(y, e, y);
+}
+
+// One 16-byte shared-memory load of a staged halo position (the compiler
+// would otherwise split it when the fourth word is not used).
+__device__ __forceinline__ uint4 lds128(const uint4 *p)
+{
+    uint4 q;
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(q.x), "=r"(q.y), "=r"(q.z), "=r"(q.w) : "r"(a));
+    return q;
+}
+
+// A tile's halo and list block by bulk (TMA) copies, issued by the 32 lanes of
+// the first warp (the force kernel and the reverse pass): lane 0 arms the staging
+// barrier with the tile's byte count, then lane q < np copies halo piece q (a
+// contiguous run of 16-byte positions) and lane np the list block, if it fits
+// the stage (64-byte aligned, read rounded up to 16 bytes; the list and the
+// stage carry that slack).  The copies go out in parallel.
+__device__ __forceinline__ void issue_tile_bulk(const Bufs &b, const Tile &tl, const Piece *pc, int np, const uint4 *P,
+                                                uint4 *hpos, unsigned short *lst, unsigned long long *bar, int lane)
+{
+    const int Pt = tl.s1 - tl.s0;
+    const unsigned lbytes = tl.kmax * Pt <= kListStage * kTileMax ? ((unsigned)(tl.kmax * Pt) * 2u + 15u) & ~15u : 0u;
+    if (lane == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (unsigned)pc[np].hoff * 16u + lbytes);
+    }
+    __syncwarp();
+    fence_proxy_async_smem();
+    if (lane < np) {
+        if (pc[lane].n > 0) bulk_g2s(&hpos[pc[lane].hoff], &P[pc[lane].slot0], (unsigned)pc[lane].n * 16u, bar);
+    } else if (lane == np && lbytes) {
+        bulk_g2s(lst, b.nbr + nbr_index(tl.s0, Pt, b.K, 0, 0), lbytes, bar);
+    }
+}
+
 // Exact conversions between FP64 and 64-bit integers by adding and removing
 // 1.5 * 2^52, whose unit in the last place is 1 (valid for |value| < 2^51).
 // They replace the integer <-> FP64 conversion instructions, which are slow
