@@ -757,10 +757,11 @@ __device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, con
 // candidate by candidate (a shared-memory broadcast per half), keeping j when
 // |d_ij| < r_cut + r_skin.  The ranges of both unions sit in the warp's table
 // `rng` ([half][range][h0, h1, j0]), so no loop below needs the other lanes:
-// the two halves run their own ranges side by side.  Candidates whose FP32
-// r^2 lies within rounding of the list radius are set aside and decided
-// afterwards in FP64 from the master positions (rare), appended after the
-// others: a lone one directly, several by walking the ranges again.  Appends are branch-free: every candidate is written at the lane's
+// the two halves run their own ranges side by side.  The walk keeps every
+// candidate whose FP32 r^2 is below the upper edge of the rounding band of
+// the list radius; a lane that kept one inside the band (rare) afterwards
+// drops those whose FP64 distance from the master positions is not below the
+// radius.  Appends are branch-free: every candidate is written at the lane's
 // next free row and the row pointer advances only on a hit.  The shared stage
 // has the final [row][particle] layout of the tile's list block; a list that
 // outgrows it is walked again straight into global memory (rare).
@@ -811,8 +812,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         unsigned short *col = own ? lst + pp : dummy + lane;
         const int stride = own ? Pt : 0;
         int cnt = 0;
-        int nband = 0;    // candidates within rounding of the list radius
-        int tie_h = 0;    // the last of them
+        bool tie = false;    // a kept candidate lies within rounding of the list radius
         for (int r = 0; r < nrng; ++r) {
             const int h1 = rng[half][r][1];
             int h = rng[half][r][0];
@@ -828,11 +828,9 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                     const float r2 = C::sep2(p, pj[u], ry, rz);
                     const int hj = C::index(pj[u], h + u);
                     const bool flt = HALF ? hj > thr : hj != self;
-                    const bool in = (r2 < lo) & flt;
-                    const bool band = (r2 < hi) & !(r2 < lo) & flt;
-                    nband += band;
-                    tie_h = band ? hj : tie_h;
-                    *q = (unsigned short)C::index(pj[u], h + u);
+                    const bool in = (r2 < hi) & flt;
+                    tie |= in & !(r2 < lo);
+                    *q = (unsigned short)hj;
                     q += in ? stride : 0;
                     cnt += in;
                 }
@@ -840,41 +838,34 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
             for (; h < h1; ++h) {
                 const float r2 = C::sep2(p, halo[h], ry, rz);
                 const bool flt = HALF ? h > thr : h != self;
-                const bool in = (r2 < lo) & flt;
-                const bool band = (r2 < hi) & !(r2 < lo) & flt;
-                nband += band;
-                tie_h = band ? h : tie_h;
+                const bool in = (r2 < hi) & flt;
+                tie |= in & !(r2 < lo);
                 col[max(min(cnt, cap - 4), 0) * stride] = (unsigned short)h;
                 cnt += in;
             }
         }
-        // candidates within rounding of the list radius: FP64, appended.  The
-        // common case is a single one, settled directly; more than one means
-        // walking the ranges again (rare)
-        const bool tie = nband > 0;
-        if (valid && nband == 1) {
-            int j = -1;
-            for (int r = 0; r < nrng; ++r) {
-                const int a = rng[half][r][0], e = rng[half][r][1];
-                if (tie_h >= a && tie_h < e) j = rng[half][r][2] + (tie_h - a);
-            }
-            if (j >= 0 && r2_fp64(X, b.S, i, j, R.L) < R.rl2) {
-                col[max(min(cnt, cap - 1), 0) * stride] = (unsigned short)tie_h;
-                ++cnt;
-            }
-        } else if (nband > 1 && valid) {
-            for (int r = 0; r < nrng; ++r) {
-                const int h0 = rng[half][r][0], h1 = rng[half][r][1], j0 = rng[half][r][2];
-                const int thr = HALF ? i - j0 + h0 : 0;
-                for (int h = h0; h < h1; ++h) {
-                    const float r2 = C::sep2(p, halo[h], ry, rz);
-                    if ((r2 < hi) & !(r2 < lo) & (HALF ? h > thr : h != self) &&
-                        r2_fp64(X, b.S, i, j0 + (h - h0), R.L) < R.rl2) {
-                        col[max(min(cnt, cap - 1), 0) * stride] = (unsigned short)h;
-                        ++cnt;
+        // The walk kept every candidate below the upper edge of the FP32
+        // rounding band of the list radius.  Where some kept candidate lies in
+        // the band (rare), the list is compacted in place: the band's entries
+        // stay only when the FP64 distance from the master positions is below
+        // the list radius.  (A list that outgrew the stage is walked again
+        // below, with the same decisions.)
+        if (valid && tie && cnt <= cap - 4) {
+            int kept = 0;
+            for (int k = 0; k < cnt; ++k) {
+                const int h = col[k * stride];
+                bool keep = C::sep2(p, halo[h], ry, rz) < lo;
+                if (!keep) {
+                    int j = -1;
+                    for (int r = 0; r < nrng; ++r) {
+                        const int a = rng[half][r][0], e = rng[half][r][1];
+                        if (h >= a && h < e) j = rng[half][r][2] + (h - a);
                     }
+                    keep = j >= 0 && r2_fp64(X, b.S, i, j, R.L) < R.rl2;
                 }
+                if (keep) col[(kept++) * stride] = (unsigned short)h;
             }
+            cnt = kept;
         }
         // a list longer than the stage allows (or a tile without a stage):
         // walk the candidates again in the same order; rows below cap go to
@@ -904,6 +895,7 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
                             put(h);
                     }
                 }
+            cnt = c2;   // the walk's count included band candidates that FP64 may reject
         }
         if (valid) {
             // pad with the particle's own index (r = 0 is never an interaction)
