@@ -88,6 +88,29 @@ def test_backward_of_final_state_loss_matches_oracle(md, precision, T, k, tol):
         assert gs[r] == pytest.approx(gs_ref, rel=tol)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 2e-4)])
+def test_backward_with_oversized_tiles_and_long_lists(md, precision, tol):
+    """r_cut = 5 sigma: cells of about 170 particles, so a tile (at least one
+    cell) holds more particles than a block has threads, and lists of about
+    520 entries, longer than the shared-memory list stage, are read from
+    global memory.  The reverse pass over these paths equals the oracle's."""
+    x, v, box = inputs.perturbed_lattice(7, T=0.8, seed=93, amp=0.1)   # 1372 particles, L = 11.8
+    n = len(x)
+    h = md.md_create(n, box, rc_over_sigma=5.0, precision=precision)
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    st = md.md_get_stats(h)
+    assert st["max_cell_occupancy"] > 128 and st["max_list_len"] > 96
+    md.md_forward(h, 6, 3, None)
+    c = np.array([loss_coefs(n, box)])
+    ge, gs = np.zeros(1), np.zeros(1)
+    md.md_backward(h, None, None, c, ge, gs)
+    s = oracle.System(n, box, rc=5.0, dt=0.005)
+    _, ge_ref, gs_ref, _, _ = oracle.vv_adjoint(s, x, v, 6, *c[0])
+    assert ge[0] == pytest.approx(ge_ref, rel=tol)
+    assert gs[0] == pytest.approx(gs_ref, rel=tol)
+
+
 def test_backward_end_point_loss_only(md):
     """dL_deuw = NULL: a loss on the final positions and velocities alone
     (host arrays), FP64 forward, against the oracle."""
