@@ -383,7 +383,7 @@ def workload_line(md, torch, dev, args, name, n, h, prep, extra, chain_kernels=N
     return line
 
 
-def run_melt(md, torch, dev, args):
+def run_melt(md, torch, dev, args, steps=None, emit=True):
     """Polymer melt: 2000 linear chains of 200 beads at bead density 0.85,
     WCA (r_cut = 2^(1/6)) on all pairs, FENE K = 30, R0 = 1.5, Langevin
     gamma = 0.5 at T = 1, dt = 0.01, skin 0.4.  Preparation (untimed): free
@@ -417,15 +417,16 @@ def run_melt(md, torch, dev, args):
     md.md_autotune(h, 10)
     prep = f"free random walks, cosine push-off A = 1..100 (7 x 300 FP64 steps), 300 WCA steps at dt 0.005: " \
            f"{time.perf_counter() - t0:.1f} s"
-    workload_line(md, torch, dev, args, "polymer melt", n, h, prep,
-                  {"workload": f"Kremer-Grest melt, 2000 x 200 linear chains (N = {n}), bead density 0.85, "
-                               f"WCA + FENE (K 30, R0 1.5) + Langevin (gamma 0.5, T 1), dt 0.01, skin 0.4",
-                   "l2": "working set about 60 MB (below L2); the timed steps run back to back"},
-                  chain_kernels=REBUILD_KERNELS + 1)
+    line = workload_line(md, torch, dev, args, "polymer melt", n, h, prep,
+                         {"workload": f"Kremer-Grest melt, 2000 x 200 linear chains (N = {n}), bead density 0.85, "
+                                      f"WCA + FENE (K 30, R0 1.5) + Langevin (gamma 0.5, T 1), dt 0.01, skin 0.4",
+                          "l2": "working set about 60 MB (below L2); the timed steps run back to back"},
+                         chain_kernels=REBUILD_KERNELS + 1, steps=steps, emit=emit)
     h.destroy()
+    return line
 
 
-def run_rings(md, torch, dev, args):
+def run_rings(md, torch, dev, args, steps=None, emit=True):
     """The paper's own polymer melt: 1600 ring polymers of 200 beads (N =
     320,000) at bead density 0.85, WCA (r_cut = 2^(1/6)) on all pairs, FENE
     (K 30, R0 1.5), the cosine angle term (K 1.5), Langevin gamma 0.5 at T 1,
@@ -461,13 +462,14 @@ def run_rings(md, torch, dev, args):
     md.md_autotune(h, 10)
     prep = f"closed random walks, cosine push-off A = 1..100 (7 x 300 FP64 steps), 300 WCA steps: " \
            f"{time.perf_counter() - t0:.1f} s"
-    workload_line(md, torch, dev, args, "ring polymer melt", n, h, prep,
-                  {"workload": f"ring polymer melt, 1600 x 200 (N = {n}), bead density 0.85, WCA + FENE "
-                               f"(K 30, R0 1.5) + cosine angle (K 1.5) + Langevin (gamma 0.5, T 1), dt 0.005, "
-                               f"skin 0.4",
-                   "l2": "working set about 50 MB (below L2); the timed steps run back to back"},
-                  chain_kernels=REBUILD_KERNELS + 1)
+    line = workload_line(md, torch, dev, args, "ring polymer melt", n, h, prep,
+                         {"workload": f"ring polymer melt, 1600 x 200 (N = {n}), bead density 0.85, WCA + FENE "
+                                      f"(K 30, R0 1.5) + cosine angle (K 1.5) + Langevin (gamma 0.5, T 1), "
+                                      f"dt 0.005, skin 0.4",
+                          "l2": "working set about 50 MB (below L2); the timed steps run back to back"},
+                         chain_kernels=REBUILD_KERNELS + 1, steps=steps, emit=emit)
     h.destroy()
+    return line
 
 
 def run_slab(md, torch, dev, args, steps=None, emit=True):
@@ -796,6 +798,8 @@ def main():
         kx = max(100, min(args.steps, 500))
         extras["slab"] = run_slab(md, torch, dev, args, steps=kx, emit=False)
         extras["sphere"] = run_sphere(md, torch, dev, args, steps=kx, emit=False)
+        extras["melt"] = run_melt(md, torch, dev, args, steps=kx, emit=False)
+        extras["rings"] = run_rings(md, torch, dev, args, steps=kx, emit=False)
 
         extras["ensemble"] = ensemble_leg(md, torch, dev)
 
