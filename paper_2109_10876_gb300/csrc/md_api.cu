@@ -57,6 +57,10 @@ struct md_handle {
     cudaGraphExec_t gexec = nullptr, gexec_e = nullptr;       // without / with energies every step
     cudaGraph_t graph_e = nullptr;
     long long gen = 0, gexec_gen = -1, gexec_e_gen = -1;   // gen: bumped whenever the kernels' buffers change
+    // the rebuild chain alone behind a conditional IF (the reverse pass's reloads)
+    cudaGraph_t graph_chain = nullptr;
+    cudaGraphExec_t gexec_chain = nullptr;
+    long long gexec_chain_gen = -1;
     bool use_graph = true;
     // md_set_recovery: md_step grows the list / halo capacity and finishes the
     // call when a rebuild inside it overflowed
@@ -345,6 +349,42 @@ bool build_step_graph(md_handle *h, bool energy)
         return false;
     if (cudaGraphInstantiate(&gexec, G, 0) != cudaSuccess) { gexec = nullptr; return false; }
     ggen = h->gen;
+    return true;
+}
+
+// The rebuild chain behind a conditional IF set from Ctl::rebuild, as one
+// graph: where the decision to rebuild is taken on the device and most calls
+// need no rebuild, one graph launch replaces the chain's kernels, each of
+// which would otherwise be launched only to return at once.
+bool build_chain_graph(md_handle *h)
+{
+    if (h->gexec_chain && h->gexec_chain_gen == h->gen) return true;
+    if (h->gexec_chain) { cudaGraphExecDestroy(h->gexec_chain); h->gexec_chain = nullptr; }
+    if (h->graph_chain) { cudaGraphDestroy(h->graph_chain); h->graph_chain = nullptr; }
+    if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+    cudaGraph_t G;
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return false;
+    h->graph_chain = G;
+    cudaGraphConditionalHandle hI;
+    if (cudaGraphConditionalHandleCreate(&hI, G, 0, 0) != cudaSuccess) return false;
+    Bufs b = h->b;
+    b.g_while = 0;
+    b.thermo = nullptr;
+    b.thermo_ring = nullptr;
+    std::vector<cudaGraphNode_t> tail;
+    if (!capture_into(h, G, {}, [&](cudaStream_t s) { mdk::launch_cond(b, hI, 0, s); }, &tail)) return false;
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hI;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t nI;
+    if (cudaGraphAddNode(&nI, G, tail.data(), nullptr, tail.size(), &ip) != cudaSuccess) return false;
+    if (!capture_into(h, ip.conditional.phGraph_out[0], {}, [&](cudaStream_t s) { mdk::launch_rebuild_chain(b, s); },
+                      nullptr))
+        return false;
+    if (cudaGraphInstantiate(&h->gexec_chain, G, 0) != cudaSuccess) { h->gexec_chain = nullptr; return false; }
+    h->gexec_chain_gen = h->gen;
     return true;
 }
 
@@ -720,6 +760,8 @@ void md_destroy(md_handle *h)
     if (h->graph) cudaGraphDestroy(h->graph);
     if (h->gexec_e) cudaGraphExecDestroy(h->gexec_e);
     if (h->graph_e) cudaGraphDestroy(h->graph_e);
+    if (h->gexec_chain) cudaGraphExecDestroy(h->gexec_chain);
+    if (h->graph_chain) cudaGraphDestroy(h->graph_chain);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -1147,7 +1189,12 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
 static md_status adj_load(md_handle *h, const double *x, cudaStream_t st)
 {
     mdk::launch_reload(h->b, x, st);
-    mdk::launch_rebuild_chain(h->b, st);
+    if (!h->timing && h->use_graph && build_chain_graph(h)) {
+        if (!cuda_ok(h, cudaGraphLaunch(h->gexec_chain, st), "graph launch")) return MD_ERR_CUDA;
+    } else {
+        cudaGetLastError();   // a failed graph build leaves nothing behind: stream launches
+        mdk::launch_rebuild_chain(h->b, st);
+    }
     h->F_valid = false;
     return cuda_ok(h, cudaGetLastError(), "reload launch") ? MD_OK : MD_ERR_CUDA;
 }
