@@ -76,6 +76,7 @@ __global__ void k_reset_ctl(Ctl *ctl)
     ctl->bad_site = 0;
     ctl->plant = 0;
     ctl->bad_index = 0;
+    ctl->step0 = 0;
 }
 
 // Caller layout (3, N) -> slot layout; initial slot order = caller order.
@@ -207,6 +208,21 @@ __global__ void k_set_steps(Ctl *ctl, long long left)
 {
     ctl->steps_left = left;
     ctl->rec = 0;
+    ctl->step0 = ctl->step;
+}
+
+// The current positions in caller order into slot step - step0 of the
+// position ring (a graph-launched md_step that records its trajectory).
+__global__ void k_record_x(Bufs b)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.S) return;
+    const int cur = b.ctl->cur;
+    const int id = (int)b.pos[cur][s].w;
+    if (id < 0) return;
+    double *out = b.xring + 3 * b.N * (b.ctl->step - b.ctl->step0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k * b.N + id] = b.x[cur][k * b.S + s];
 }
 
 // ---------------------------------------------------------------- counting sort
@@ -1165,6 +1181,8 @@ void launch_force_by_id(const Bufs &b, double *buf, int dir, cudaStream_t st)
     k_force_by_id<<<(unsigned)((b.S + 255) / 256), 256, 0, st>>>(b, buf, dir);
 }
 void launch_set_steps(const Bufs &b, long long left, cudaStream_t st) { k_set_steps<<<1, 1, 0, st>>>(b.ctl, left); }
+
+void launch_record_x(const Bufs &b, cudaStream_t st) { k_record_x<<<b.nblk, kBlock, 0, st>>>(b); }
 
 static int list_grid(size_t smem)
 {

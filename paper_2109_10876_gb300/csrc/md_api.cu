@@ -57,6 +57,11 @@ struct md_handle {
     cudaGraphExec_t gexec = nullptr, gexec_e = nullptr;       // without / with energies every step
     cudaGraph_t graph_e = nullptr;
     long long gen = 0, gexec_gen = -1, gexec_e_gen = -1;   // gen: bumped whenever the kernels' buffers change
+    // the step graph that also records the positions after every step (the
+    // reverse pass's segment re-runs, into ad_seg)
+    cudaGraph_t graph_x = nullptr;
+    cudaGraphExec_t gexec_x = nullptr;
+    long long gexec_x_gen = -1;
     // the rebuild chain alone behind a conditional IF (the reverse pass's reloads)
     cudaGraph_t graph_chain = nullptr;
     cudaGraphExec_t gexec_chain = nullptr;
@@ -280,12 +285,14 @@ bool capture_into(md_handle *h, cudaGraph_t g, const std::vector<cudaGraphNode_t
 //   -> fused force } -> cond(I2) -> IF(I2) { rebuild chain } -> final force.
 // The fused kernel's last block counts the steps down and sets W; with
 // energies, each force kernel's last block writes its record to the next slot
-// of the thermo buffer.
-bool build_step_graph(md_handle *h, bool energy)
+// of the thermo buffer.  With `record` (no energies), the positions after the
+// kick-drift and after every fused force are written to the slots of the
+// reverse pass's segment buffer (k_record_x, slot = steps since the call began).
+bool build_step_graph(md_handle *h, bool energy, bool record = false)
 {
-    cudaGraphExec_t &gexec = energy ? h->gexec_e : h->gexec;
-    cudaGraph_t &graph = energy ? h->graph_e : h->graph;
-    long long &ggen = energy ? h->gexec_e_gen : h->gexec_gen;
+    cudaGraphExec_t &gexec = record ? h->gexec_x : energy ? h->gexec_e : h->gexec;
+    cudaGraph_t &graph = record ? h->graph_x : energy ? h->graph_e : h->graph;
+    long long &ggen = record ? h->gexec_x_gen : energy ? h->gexec_e_gen : h->gexec_gen;
     if (gexec && ggen == h->gen) return true;
     if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
     if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
@@ -300,10 +307,12 @@ bool build_step_graph(md_handle *h, bool energy)
     b.g_while = 0;
     b.thermo = nullptr;
     b.thermo_ring = energy ? h->thermo_stage : nullptr;
+    b.xring = record ? h->ad_seg : nullptr;
     const int prec = h->precision;
     std::vector<cudaGraphNode_t> tail;
     if (!capture_into(h, G, {}, [&](cudaStream_t s) {
             mdk::launch_kick_drift(b, s);
+            if (record) mdk::launch_record_x(b, s);
             mdk::launch_cond(b, hW, 1, s);
         }, &tail))
         return false;
@@ -330,8 +339,10 @@ bool build_step_graph(md_handle *h, bool energy)
         return false;
     Bufs bf = b;
     bf.g_while = hW;
-    if (!capture_into(h, BW, {nI}, [&](cudaStream_t s) { mdk::launch_force(bf, prec, mdk::kModeFused, energy, s); },
-                      nullptr))
+    if (!capture_into(h, BW, {nI}, [&](cudaStream_t s) {
+            mdk::launch_force(bf, prec, mdk::kModeFused, energy, s);
+            if (record) mdk::launch_record_x(b, s);
+        }, nullptr))
         return false;
     if (!capture_into(h, G, {nW}, [&](cudaStream_t s) { mdk::launch_cond(b, hI2, 0, s); }, &tail)) return false;
     cudaGraphNodeParams ip2 = {};
@@ -762,6 +773,8 @@ void md_destroy(md_handle *h)
     if (h->graph_e) cudaGraphDestroy(h->graph_e);
     if (h->gexec_chain) cudaGraphExecDestroy(h->gexec_chain);
     if (h->graph_chain) cudaGraphDestroy(h->graph_chain);
+    if (h->gexec_x) cudaGraphExecDestroy(h->gexec_x);
+    if (h->graph_x) cudaGraphDestroy(h->graph_x);
     if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
@@ -1186,6 +1199,36 @@ md_status md_forward(md_handle *h, int32_t nsteps, int32_t ckpt_every, double *e
 // set the handle's state from caller-order device arrays and build its lists
 // Positions x (caller order, device) into the particles' current slots; the
 // Verlet list is rebuilt only if the displacement since its build asks for it.
+// The steps of a checkpoint segment again, with the positions after each
+// step in slots 1..nsteps of ad_seg: one graph launch of md_step's loop with a
+// recording node after every drift (step by step with section timers, without
+// graphs, or with overflow recovery, whose md_step calls synchronise).
+static md_status step_record(md_handle *h, int nsteps, cudaStream_t st)
+{
+    if (nsteps <= 0) return MD_OK;
+    md_status s = first_build(h, st);
+    if (s != MD_OK) return s;
+    const long long n3 = 3 * h->N;
+    if (!h->timing && !h->recover && h->use_graph && build_step_graph(h, false, true)) {
+        Bufs b = h->b;
+        if (!h->F_valid) {
+            mdk::launch_rebuild_chain(b, st);
+            mdk::launch_force(b, h->precision, mdk::kModeStore, false, st);
+        }
+        mdk::launch_set_steps(b, (long long)nsteps - 1, st);
+        if (!cuda_ok(h, cudaGraphLaunch(h->gexec_x, st), "graph launch")) return MD_ERR_CUDA;
+        h->F_valid = true;
+        return MD_OK;
+    }
+    cudaGetLastError();   // a failed graph build leaves nothing behind
+    for (int t = 1; t <= nsteps; ++t) {
+        s = md_step(h, 1, 0, nullptr, st);
+        if (s != MD_OK) return s;
+        mdk::launch_get_state(h->b, h->ad_seg + (long long)t * n3, nullptr, st);
+    }
+    return MD_OK;
+}
+
 static md_status adj_load(md_handle *h, const double *x, cudaStream_t st)
 {
     mdk::launch_reload(h->b, x, st);
@@ -1213,6 +1256,7 @@ md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, co
         h->ad_seg = grow(h, h->ad_seg, (size_t)((k + 1) * n3));
         if (!h->ad_seg) return fail(h, MD_ERR_CUDA, "cannot allocate");
         h->ad_seg_cap = k + 1;
+        h->gen++;   // the recording step graph holds the buffer's address
     }
     if (!h->ad_small && !(h->ad_small = dalloc<double>(h, (size_t)(12 * nrep)))) return fail(h, MD_ERR_CUDA, "cannot allocate");
     if (h->precision == MD_FP32_FIXED && !h->b.adj_wa) {
@@ -1262,11 +1306,8 @@ md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, co
             if (s != MD_OK) return s;
             if (!cuda_ok(h, cudaMemcpyAsync(h->ad_seg, ck, sizeof(double) * n3, cudaMemcpyDeviceToDevice, st), "copy"))
                 return MD_ERR_CUDA;
-            for (int t = t0 + 1; t <= t1; ++t) {
-                s = md_step(h, 1, 0, nullptr, stream);
-                if (s != MD_OK) return s;
-                mdk::launch_get_state(h->b, h->ad_seg + (long long)(t - t0) * n3, nullptr, st);
-            }
+            s = step_record(h, t1 - t0, st);
+            if (s != MD_OK) return s;
             for (int t = t1; t >= (c == 0 ? 0 : t0 + 1); --t) {
                 s = adj_load(h, h->ad_seg + (long long)(t - t0) * n3, st);
                 if (s != MD_OK) return s;

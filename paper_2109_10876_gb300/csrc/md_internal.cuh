@@ -120,6 +120,7 @@ struct Ctl {
     int bad_site;            // checked build: the first failing bounds check (CheckSite), else 0
     int plant;               // checked build: a site whose next checks are made to fail (self-test), else 0
     long long bad_index;     // checked build: the index that failed at bad_site
+    long long step0;         // Ctl::step at the start of a graph-launched md_step (set by k_set_steps)
 };
 
 #ifdef MD_CHECKED
@@ -268,6 +269,8 @@ struct Bufs {
     double *thermo;          // where the last block writes (U, K, W) per replica, or null
     double *thermo_ring;     // graph-launched md_step: record Ctl::rec goes to thermo_ring + 3 nrep rec
     double *fout;            // force output in caller order (3 * N) or null
+    double *xring;           // positions recorded after every step of a graph-launched call: slot
+                             // step - step0 at xring + 3 N (step - step0), caller order (or null)
     Ctl *ctl;
     long long S, N;
     int C, K, nrep, nblk;
@@ -522,6 +525,8 @@ void launch_set_rebuild(const Bufs &b, cudaStream_t st);
 // graph conditionals: set `handle` to (ctl->rebuild != 0) (what = 0) or (ctl->steps_left > 0) (what = 1)
 void launch_cond(const Bufs &b, unsigned long long handle, int what, cudaStream_t st);
 void launch_set_steps(const Bufs &b, long long left, cudaStream_t st);
+// the current positions, in caller order, into slot Ctl::step - Ctl::step0 of b.xring
+void launch_record_x(const Bufs &b, cudaStream_t st);
 // one block waiting on a barrier that nothing completes, `polls` polls at most
 void launch_wait_selftest(const Bufs &b, int polls, cudaStream_t st);
 void launch_adj_hvp(const Bufs &b, int precision, const double *w, double *hv, double scale, double *g,
