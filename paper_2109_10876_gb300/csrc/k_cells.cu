@@ -391,42 +391,75 @@ __device__ __forceinline__ void reorder_move(const Bufs &b, int cur, int nxt, in
     b.cellid[dst] = c;
 }
 
+// One cell by a whole warp: ranks by shuffles for up to 32 members, by a
+// loop over the members beyond.
+__device__ __noinline__ void reorder_cell_warp(const Bufs &b, int cur, int nxt, int c, int lane)
+{
+    const uint4 *pin = b.pos[cur];
+    const int start = b.cell_start[c], n = b.cell_end[c] - start;
+    if (n <= 32) {
+        const bool act = lane < n;
+        int s = act ? b.bucket[start + lane] : 0;
+        if (act && !md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
+        const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
+        const unsigned long long key = act ? order_key(p) : ~0ULL;
+        int rank = 0;
+        for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, key, q) < key);
+        if (act) reorder_move(b, cur, nxt, c, s, start + rank, p);
+        return;
+    }
+    for (int m = lane; m < n; m += 32) {
+        int s = b.bucket[start + m];
+        if (!md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
+        uint4 p = pin[s];
+        const unsigned long long key = order_key(p);
+        int rank = 0;
+        for (int q = 0; q < n; ++q) {
+            int sq = b.bucket[start + q];
+            if (!md_ok(b.ctl, sq >= 0 && sq < b.S, kSiteReorder, sq)) sq = 0;
+            rank += (order_key(pin[sq]) < key);
+        }
+        reorder_move(b, cur, nxt, c, s, start + rank, p);
+    }
+}
+
+// A warp takes four cells at a time: a cell of at most 8 members is ordered
+// by its own 8 lanes (ranks by shuffles within the group; keys are unique and
+// idle lanes hold the largest), and the group's larger cells go to the whole
+// warp one after another.  Sparse systems (a melt's three particles per cell,
+// a vapour's fraction of one) then keep most lanes busy.
 __global__ void k_reorder(Bufs b)
 {
     if (!b.ctl->rebuild || b.ctl->err) return;
-    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
     const int cur = b.ctl->cur, nxt = cur ^ 1;
     const uint4 *pin = b.pos[cur];
-    // a bounded grid of warps strides over the cells
+    // a bounded grid of warps strides over groups of four cells
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < b.C; gw += nw) {
-        const int c = (int)gw;
-        const int start = b.cell_start[c], end = b.cell_end[c];
-        const int n = end - start;
-        if (lane == 0) b.cell_count[c] = 0;   // histogram is clean for the next build
-        if (n <= 32) {
-            const bool act = lane < n;
-            int s = act ? b.bucket[start + lane] : 0;
-            if (act && !md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
-            const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
-            const unsigned long long key = act ? order_key(p) : ~0ULL;
-            int rank = 0;
-            for (int q = 0; q < n; ++q) rank += (__shfl_sync(0xffffffffu, key, q) < key);
-            if (act) reorder_move(b, cur, nxt, c, s, start + rank, p);
-            continue;
+    for (long long c0 = 4 * (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); c0 < b.C; c0 += 4 * nw) {
+        const long long cl = c0 + g;
+        int start = 0, n = 0;
+        if (cl < b.C) {
+            start = b.cell_start[cl];
+            n = b.cell_end[cl] - start;
+            if (gl == 0) b.cell_count[cl] = 0;   // histogram is clean for the next build
         }
-        for (int m = lane; m < n; m += 32) {
-            int s = b.bucket[start + m];
-            if (!md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
-            uint4 p = pin[s];
-            const unsigned long long key = order_key(p);
-            int rank = 0;
-            for (int q = 0; q < n; ++q) {
-                int sq = b.bucket[start + q];
-                if (!md_ok(b.ctl, sq >= 0 && sq < b.S, kSiteReorder, sq)) sq = 0;
-                rank += (order_key(pin[sq]) < key);
-            }
-            reorder_move(b, cur, nxt, c, s, start + rank, p);
+        const bool small = cl < b.C && n <= 8;
+        const bool act = small && gl < n;
+        int s = act ? b.bucket[start + gl] : 0;
+        if (act && !md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
+        const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
+        const unsigned long long key = act ? order_key(p) : ~0ULL;
+        int rank = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rank += (__shfl_sync(full, key, (lane & ~7) | q) < key);
+        if (act) reorder_move(b, cur, nxt, (int)cl, s, start + rank, p);
+        unsigned big = __ballot_sync(full, gl == 0 && cl < b.C && !small);
+        while (big) {
+            const int lead = __ffs(big) - 1;
+            big &= big - 1;
+            reorder_cell_warp(b, cur, nxt, (int)(c0 + (lead >> 3)), lane);
         }
     }
 }
@@ -1223,7 +1256,7 @@ void launch_rebuild_chain(const Bufs &b, cudaStream_t st)
     k_scan_top<<<1, kScanThreads, 0, st>>>(b);
     k_scan_write<<<nsb, kScanBlock, 0, st>>>(b);
     k_scatter<<<chain_grid(b.nblk), kBlock, 0, st>>>(b);
-    k_reorder<<<chain_grid(blocks_for((long long)b.C * 32, 256)), 256, 0, st>>>(b);
+    k_reorder<<<chain_grid(blocks_for((long long)b.C * 8, 256)), 256, 0, st>>>(b);
     const long long nt = b.n_bond_ent > b.n_ang_ent ? b.n_bond_ent : b.n_ang_ent;
     if (nt > 0) k_topology_slots<<<blocks_for(nt, 256), 256, 0, st>>>(b);
     k_tile_count<<<blocks_for(b.nrows, kTileWarps), 32 * kTileWarps, 0, st>>>(b);
