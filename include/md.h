@@ -302,9 +302,10 @@ md_status md_backward(md_handle *h, const double *dL_dx, const double *dL_dv, co
 md_status md_export_pairs(md_handle *h, int32_t *pairs_out, int64_t capacity, int64_t *n_out, void *stream);
 
 /* Pick the tile size (particles per tile of the force and list kernels) by
- * timing: starting from the largest (128), halve it while trial_steps steps
- * get faster, down to 8.  This is the GPU counterpart of the paper's tuning of
- * the HPX subnode count (Sec. 3.3, Sec. 4.2), which doubles the number of
+ * timing trial_steps steps at each candidate: from the largest (128) down to
+ * 64 in steps of 16, all of them, then halving while the steps get faster, down
+ * to 8; the fastest is kept.  This is the GPU counterpart of the paper's tuning
+ * of the HPX subnode count (Sec. 3.3, Sec. 4.2), which doubles the number of
  * subnodes until the elapsed time of a few steps stops falling.  Positions,
  * velocities, the stored force and the step counter are saved and restored,
  * so the trajectory goes on from where it was (bit for bit in

@@ -1398,8 +1398,13 @@ md_status md_autotune(md_handle *h, int32_t trial_steps, int32_t *tile_max_out, 
     float best_ms = 0.f;
     int best = h->b.tile_max;
     md_status s = MD_OK;
-    // the sweep of the paper's subnode count: halve the task size while it helps
-    for (int cap = mdk::kTileMax; cap >= 8; cap /= 2) {
+    // the sweep of the paper's subnode count, from the largest task size: in
+    // steps of 16 particles down to 64, every size tried (neighbouring sizes can
+    // differ by less than a trial's noise, and a size that splits rows of cells
+    // more evenly can win further down), then halving while it helps
+    static const int kCands[] = {mdk::kTileMax, 112, 96, 80, 64, 32, 16, 8};
+    for (int ci = 0; ci < (int)(sizeof(kCands) / sizeof(kCands[0])); ++ci) {
+        const int cap = kCands[ci];
         if ((s = md_set_tile_size(h, cap, stream)) != MD_OK) break;
         if ((s = md_set_state(h, save, save + n3, st)) != MD_OK) break;
         if ((s = md_build_neighbors(h, stream)) != MD_OK) break;
@@ -1410,8 +1415,8 @@ md_status md_autotune(md_handle *h, int32_t trial_steps, int32_t *tile_max_out, 
         if ((s = sync_and_check(h, st)) != MD_OK) break;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (cap == mdk::kTileMax || ms < best_ms) { best_ms = ms; best = cap; }
-        else break;
+        if (ci == 0 || ms < best_ms) { best_ms = ms; best = cap; }
+        else if (cap <= 64) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

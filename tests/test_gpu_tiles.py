@@ -60,7 +60,7 @@ def test_pairs_and_forces_every_tile_size(md, fluid):
     md.md_set_state(h, dev(x), dev(v))
     ref = None
     tiles = []
-    for size in (128, 64, 32, 16, 8, 1):
+    for size in (128, 112, 96, 80, 64, 32, 16, 8, 1):
         md.md_set_tile_size(h, size)
         md.md_build_neighbors(h)
         np.testing.assert_array_equal(md.export_pairs_sorted(h), want_pairs)
@@ -108,7 +108,7 @@ def test_autotune_keeps_the_trajectory(md, fluid):
     md.md_build_neighbors(h2)
     md.md_step(h2, 10)
     chosen = md.md_autotune(h2, 5)
-    assert chosen in (128, 64, 32, 16, 8)
+    assert chosen in (128, 112, 96, 80, 64, 32, 16, 8)
     st = md.md_get_stats(h2)
     assert st["tile_size"] == chosen and st["steps"] == 10
     md.md_step(h2, 10)
