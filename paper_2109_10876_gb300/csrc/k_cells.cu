@@ -391,12 +391,12 @@ __device__ __forceinline__ void reorder_move(const Bufs &b, int cur, int nxt, in
     b.cellid[dst] = c;
 }
 
-// One cell by a whole warp: ranks by shuffles for up to 32 members, by a
-// loop over the members beyond.
-__device__ __noinline__ void reorder_cell_warp(const Bufs &b, int cur, int nxt, int c, int lane)
+// One cell (first slot start, n members) by a whole warp: ranks by shuffles
+// for up to 32 members, by a loop over the members beyond.
+__device__ __forceinline__ void reorder_cell_warp(const Bufs &b, int cur, int nxt, int c, int start, int n,
+                                                  int lane)
 {
     const uint4 *pin = b.pos[cur];
-    const int start = b.cell_start[c], n = b.cell_end[c] - start;
     if (n <= 32) {
         const bool act = lane < n;
         int s = act ? b.bucket[start + lane] : 0;
@@ -446,20 +446,23 @@ __global__ void k_reorder(Bufs b)
             if (gl == 0) b.cell_count[cl] = 0;   // histogram is clean for the next build
         }
         const bool small = cl < b.C && n <= 8;
-        const bool act = small && gl < n;
-        int s = act ? b.bucket[start + gl] : 0;
-        if (act && !md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
-        const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
-        const unsigned long long key = act ? order_key(p) : ~0ULL;
-        int rank = 0;
+        if (__any_sync(full, small)) {   // warp-uniform: a dense system skips this part
+            const bool act = small && gl < n;
+            int s = act ? b.bucket[start + gl] : 0;
+            if (act && !md_ok(b.ctl, s >= 0 && s < b.S, kSiteReorder, s)) s = 0;
+            const uint4 p = act ? pin[s] : make_uint4(0u, 0u, 0u, 0u);
+            const unsigned long long key = act ? order_key(p) : ~0ULL;
+            int rank = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) rank += (__shfl_sync(full, key, (lane & ~7) | q) < key);
-        if (act) reorder_move(b, cur, nxt, (int)cl, s, start + rank, p);
+            for (int q = 0; q < 8; ++q) rank += (__shfl_sync(full, key, (lane & ~7) | q) < key);
+            if (act) reorder_move(b, cur, nxt, (int)cl, s, start + rank, p);
+        }
         unsigned big = __ballot_sync(full, gl == 0 && cl < b.C && !small);
         while (big) {
             const int lead = __ffs(big) - 1;
             big &= big - 1;
-            reorder_cell_warp(b, cur, nxt, (int)(c0 + (lead >> 3)), lane);
+            const int bs = __shfl_sync(full, start, lead), bn = __shfl_sync(full, n, lead);
+            reorder_cell_warp(b, cur, nxt, (int)(c0 + (lead >> 3)), bs, bn, lane);
         }
     }
 }
