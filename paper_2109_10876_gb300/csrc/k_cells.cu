@@ -527,7 +527,72 @@ __device__ int walk_row(const Bufs &b, int g, Tile *out, int *colsum, int *own)
     }
     __syncwarp();
     int nt = 0;
-    if (lane == 0) {
+    if (in_smem) {
+        // inclusive prefix sums of the column halo counts and of the row's own
+        // counts, in place: the greedy cut below then needs no serial walk
+        const unsigned full = 0xffffffffu;
+        int carry_c = 0, carry_o = 0;
+        for (int base = 0; base < nx; base += 32) {
+            const int x = base + lane;
+            int vc = x < nx ? colsum[x] : 0, vo = x < nx ? own[x] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int tc = __shfl_up_sync(full, vc, o), to = __shfl_up_sync(full, vo, o);
+                if (lane >= o) { vc += tc; vo += to; }
+            }
+            vc += carry_c;
+            vo += carry_o;
+            if (x < nx) { colsum[x] = vc; own[x] = vo; }
+            carry_c = __shfl_sync(full, vc, 31);
+            carry_o = __shfl_sync(full, vo, 31);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            // tile [x0, x1): P = its own particles, H = the halo columns x0 - 1 .. x1
+            // (wrapped), or the whole row's halo where that many columns reach round
+            // it.  Both only grow with x1, so the greedy end of a tile (the largest
+            // x1 that keeps P <= tile_max and H <= hcap, and at least one cell) is
+            // found by a binary search.
+            const int *PC = colsum, *PO = own;
+            const int total = PC[nx - 1];
+            auto pc_at = [&](int x) -> int { return x < 0 ? 0 : PC[x]; };
+            auto halo = [&](int x0, int x1) -> int {
+                if (x1 - x0 + 2 >= nx) return total;
+                int a = x0 - 1, e = x1, h = 0;
+                if (a < 0) { h += PC[nx - 1] - PC[nx - 2]; a = 0; }
+                if (e >= nx) { h += PC[0]; e = nx - 1; }
+                return h + PC[e] - pc_at(a - 1);
+            };
+            auto fits = [&](int x0, int x1) -> bool {
+                return PO[x1 - 1] - (x0 > 0 ? PO[x0 - 1] : 0) <= b.tile_max && halo(x0, x1) <= b.hcap;
+            };
+            int x0 = 0;
+            while (x0 < nx) {
+                int x1 = x0 + 1;
+                if (fits(x0, x1)) {
+                    int lo = x1, hi = nx;
+                    while (lo < hi) {
+                        const int m = (lo + hi + 1) >> 1;
+                        if (fits(x0, m)) lo = m; else hi = m - 1;
+                    }
+                    x1 = lo;
+                }
+                if (out && md_ok(b.ctl, (out - b.tiles) + nt < b.C, kSiteTileWrite, (out - b.tiles) + nt)) {
+                    const int base = R.cell_off + (cz * ny + cy) * nx;
+                    Tile t;
+                    t.rep = r; t.cy = cy; t.cz = cz; t.x0 = x0; t.x1 = x1;
+                    t.s0 = b.cell_start[base + x0];
+                    t.s1 = b.cell_end[base + x1 - 1];
+                    t.hsize = halo(x0, x1);
+                    t.kmax = 0;
+                    out[nt] = t;
+                }
+                ++nt;
+                x0 = x1;
+            }
+        }
+    } else if (lane == 0) {
+        // a row wider than the shared arrays: the serial walk over its columns
         auto col = [&](int x) -> int {
             if (in_smem) return colsum[x];
             int sum = 0;
