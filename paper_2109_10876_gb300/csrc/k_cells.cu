@@ -882,6 +882,40 @@ __device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, con
     }
 }
 
+// The tile-relative form of union_range: lane q takes halo piece q (a run of
+// consecutive cells of one halo row, sorted along x) and keeps the entries whose
+// x lies in the group's window [x of its first particle - w, x of its last + w],
+// by two binary searches over the piece.  The window lies within the cells one
+// left of the group's first cell to one right of its last (the cell edge is at
+// least the list radius), so these are the candidates of the cell ranges
+// trimmed to the window, found without the cells' slot bounds from global memory.
+__device__ __forceinline__ void union_range_rel(const Bufs &b, const Replica &R, const Piece *pc, int np,
+                                                const float4 *halo, int hfirst, int g0, int g1, int lane,
+                                                int &rh0, int &rh1, int &rj0)
+{
+    rh0 = rh1 = rj0 = 0;
+    if (g0 > g1 || lane >= np) return;
+    const Piece q = pc[lane];
+    if (q.n <= 0) return;
+    const float xlo = halo[hfirst + g0].x - R.rl_win_u;
+    const float xhi = halo[hfirst + g1].x + R.rl_win_u;
+    int a = q.hoff, e = q.hoff + q.n;
+    while (a < e) {
+        const int m = (a + e) >> 1;
+        if (halo[m].x < xlo) a = m + 1; else e = m;
+    }
+    int a2 = a;
+    e = q.hoff + q.n;
+    while (a2 < e) {
+        const int m = (a2 + e) >> 1;
+        if (halo[m].x <= xhi) a2 = m + 1; else e = m;
+    }
+    if (!md_ok(b.ctl, a >= 0 && a2 <= pc[np].hoff, kSiteListRange, a2)) return;
+    rh0 = a;
+    rh1 = a2;
+    rj0 = q.slot0 + (a - q.hoff);
+}
+
 // Verlet lists of one tile (Sec. 2.1.2).  Each half-warp takes 16
 // consecutive particles and walks the union of their 27-cell stencils,
 // candidate by candidate (a shared-memory broadcast per half), keeping j when
@@ -913,7 +947,9 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
     int ly, cntY, lz, cntZ;
     axis_offsets(R.ncell[1], ly, cntY);
     axis_offsets(R.ncell[2], lz, cntZ);
-    const int nrng = 2 * cntY * cntZ;
+    // ranges per group: one per halo piece in the tile-relative form, else one
+    // per (halo row, side of the periodic boundary)
+    const int nrng = REL ? np : 2 * cntY * cntZ;
     const float lo = R.rl2_lo_u, hi = R.rl2_hi_u;
     const int Pt = tl.s1 - tl.s0;
     // stage rows of this tile (0: no stage, every list goes to global memory)
@@ -928,9 +964,13 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         const int i = tl.s0 + (valid ? pp : c0);
         {
             int h0, h1, j0;
-            union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0, err);
+            if constexpr (REL) union_range_rel(b, R, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0);
+            else union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0, err);
             if (lane < nrng) { rng[0][lane][0] = h0; rng[0][lane][1] = h1; rng[0][lane][2] = j0; }
-            union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0, err);
+            if constexpr (REL)
+                union_range_rel(b, R, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0);
+            else
+                union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0, err);
             if (lane < nrng) { rng[1][lane][0] = h0; rng[1][lane][1] = h1; rng[1][lane][2] = j0; }
         }
         __syncwarp();
