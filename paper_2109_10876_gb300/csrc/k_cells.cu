@@ -882,38 +882,46 @@ __device__ __forceinline__ void union_range(const Bufs &b, const Replica &R, con
     }
 }
 
-// The tile-relative form of union_range: lane q takes halo piece q (a run of
-// consecutive cells of one halo row, sorted along x) and keeps the entries whose
-// x lies in the group's window [x of its first particle - w, x of its last + w],
-// by two binary searches over the piece.  The window lies within the cells one
-// left of the group's first cell to one right of its last (the cell edge is at
-// least the list radius), so these are the candidates of the cell ranges
-// trimmed to the window, found without the cells' slot bounds from global memory.
-__device__ __forceinline__ void union_range_rel(const Bufs &b, const Replica &R, const Piece *pc, int np,
-                                                const float4 *halo, int hfirst, int g0, int g1, int lane,
-                                                int &rh0, int &rh1, int &rj0)
+// The tile-relative form of union_range, for both groups of a warp at once:
+// lane q takes halo piece q (a run of consecutive cells of one halo row, sorted
+// along x) and keeps, for each group, the entries whose x lies in the group's
+// window [x of its first particle - w, x of its last + w].  The window lies
+// within the cells one left of the group's first cell to one right of its last
+// (the cell edge is at least the list radius), so these are the candidates of
+// the cell ranges trimmed to the window, found without the cells' slot bounds
+// from global memory.  The four bounds (two per group) are counts of entries
+// below a value, taken in lockstep by power-of-two steps (a fixed number of
+// steps for the piece, no branches), so their shared-memory reads overlap.
+__device__ __forceinline__ void union_ranges_rel(const Bufs &b, const Replica &R, const Piece *pc, int np,
+                                                 const float4 *halo, int hfirst, int c0, int Pt, int lane,
+                                                 int (*rng)[kMaxPieces][3])
 {
-    rh0 = rh1 = rj0 = 0;
-    if (g0 > g1 || lane >= np) return;
-    const Piece q = pc[lane];
-    if (q.n <= 0) return;
-    const float xlo = halo[hfirst + g0].x - R.rl_win_u;
-    const float xhi = halo[hfirst + g1].x + R.rl_win_u;
-    int a = q.hoff, e = q.hoff + q.n;
-    while (a < e) {
-        const int m = (a + e) >> 1;
-        if (halo[m].x < xlo) a = m + 1; else e = m;
+    int r[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    if (lane < np && pc[lane].n > 0) {
+        const Piece q = pc[lane];
+        const float w = R.rl_win_u;
+        const int g0a = c0, g1a = min(c0 + 15, Pt - 1), g0b = c0 + 16, g1b = min(c0 + 31, Pt - 1);
+        const bool vb = g0b <= g1b;
+        const float loA = halo[hfirst + g0a].x - w, hiA = halo[hfirst + g1a].x + w;
+        const float loB = vb ? halo[hfirst + g0b].x - w : loA, hiB = vb ? halo[hfirst + g1b].x + w : hiA;
+        const float4 *x = halo + q.hoff;
+        const int n = q.n;
+        int cA0 = 0, cA1 = 0, cB0 = 0, cB1 = 0;   // entries with x < loA, x <= hiA, x < loB, x <= hiB
+        for (int step = 1 << (31 - __clz(n)); step > 0; step >>= 1) {
+            if (cA0 + step <= n && x[cA0 + step - 1].x < loA) cA0 += step;
+            if (cA1 + step <= n && x[cA1 + step - 1].x <= hiA) cA1 += step;
+            if (cB0 + step <= n && x[cB0 + step - 1].x < loB) cB0 += step;
+            if (cB1 + step <= n && x[cB1 + step - 1].x <= hiB) cB1 += step;
+        }
+        if (md_ok(b.ctl, cA0 <= cA1 && cB0 <= cB1 && q.hoff + n <= pc[np].hoff, kSiteListRange, q.hoff + n)) {
+            r[0][0] = q.hoff + cA0; r[0][1] = q.hoff + cA1; r[0][2] = q.slot0 + cA0;
+            if (vb) { r[1][0] = q.hoff + cB0; r[1][1] = q.hoff + cB1; r[1][2] = q.slot0 + cB0; }
+        }
     }
-    int a2 = a;
-    e = q.hoff + q.n;
-    while (a2 < e) {
-        const int m = (a2 + e) >> 1;
-        if (halo[m].x <= xhi) a2 = m + 1; else e = m;
+    if (lane < np) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { rng[0][lane][k] = r[0][k]; rng[1][lane][k] = r[1][k]; }
     }
-    if (!md_ok(b.ctl, a >= 0 && a2 <= pc[np].hoff, kSiteListRange, a2)) return;
-    rh0 = a;
-    rh1 = a2;
-    rj0 = q.slot0 + (a - q.hoff);
 }
 
 // Verlet lists of one tile (Sec. 2.1.2).  Each half-warp takes 16
@@ -962,15 +970,13 @@ __device__ __forceinline__ void cells_of_tile(const Bufs &b, const Replica &R, c
         const int pp = c0 + lane;
         const bool valid = pp < Pt;
         const int i = tl.s0 + (valid ? pp : c0);
-        {
+        if constexpr (REL) {
+            union_ranges_rel(b, R, pc, np, halo, hfirst, c0, Pt, lane, rng);
+        } else {
             int h0, h1, j0;
-            if constexpr (REL) union_range_rel(b, R, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0);
-            else union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0, err);
+            union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0, min(c0 + 15, Pt - 1), lane, h0, h1, j0, err);
             if (lane < nrng) { rng[0][lane][0] = h0; rng[0][lane][1] = h1; rng[0][lane][2] = j0; }
-            if constexpr (REL)
-                union_range_rel(b, R, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0);
-            else
-                union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0, err);
+            union_range<REL>(b, R, tl, pc, np, halo, hfirst, c0 + 16, min(c0 + 31, Pt - 1), lane, h0, h1, j0, err);
             if (lane < nrng) { rng[1][lane][0] = h0; rng[1][lane][1] = h1; rng[1][lane][2] = j0; }
         }
         __syncwarp();
