@@ -1190,6 +1190,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_build_list(Bufs b)
             const unsigned cx = (unsigned)((((unsigned long long)(tl.x0 + tl.x1)) << 31) / (unsigned)R.ncell[0]);
             const unsigned cy = (unsigned)((((unsigned long long)(2 * tl.cy + 1)) << 31) / (unsigned)R.ncell[1]);
             const unsigned cz = (unsigned)((((unsigned long long)(2 * tl.cz + 1)) << 31) / (unsigned)R.ncell[2]);
+#pragma unroll 4
             for (int h = threadIdx.x; h < H; h += blockDim.x) {
                 const uint4 q = halo[h];
                 halof[h] = make_float4((float)(int)(q.x - cx), (float)(int)(q.y - cy) * R.ry,
