@@ -300,7 +300,7 @@ __device__ __forceinline__ void hvp_particle(const Bufs &b, const Replica &R, co
     const float eps24 = 24.0f * (float)R.eps, sig2 = (float)(R.sigma * R.sigma), isig = (float)(1.0 / R.sigma);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 z2 = make_float2(0.f, 0.f);
-    int nband = 0;
+    bool band = false;   // a pair within rounding of r_cut
     for (int k0 = 0; k0 < npad; k0 += 4) {
         int hh[4];
 #pragma unroll
@@ -318,7 +318,7 @@ __device__ __forceinline__ void hvp_particle(const Bufs &b, const Replica &R, co
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             // padding entries are the particle itself (r^2 = 0)
             const bool in0 = (r2.x < lo) & (r2.x > 0.0f), in1 = (r2.y < lo) & (r2.y > 0.0f);
-            nband += ((r2.x < hi) & !(r2.x < lo)) + ((r2.y < hi) & !(r2.y < lo));
+            band |= ((r2.x < hi) & !(r2.x < lo)) | ((r2.y < hi) & !(r2.y < lo));
             float2 ir2 = make_float2(rcp_approx_f(r2.x), rcp_approx_f(r2.y));
             ir2.x = in0 ? ir2.x : 0.0f;
             ir2.y = in1 ? ir2.y : 0.0f;
@@ -328,7 +328,7 @@ __device__ __forceinline__ void hvp_particle(const Bufs &b, const Replica &R, co
             hvp_pair2(dx, dy, dz, ir2, wa0, wb0, wa1, wb1, wai, wbi, sig2, eps24, isig, a);
         }
     }
-    if (nband) {
+    if (band) {
         // pairs within rounding of r_cut: membership decided in FP64 from the
         // master positions; each as one lane of a packed pair (the other masked)
         for (int k = 0; k < n; ++k) {

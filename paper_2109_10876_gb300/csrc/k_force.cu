@@ -430,8 +430,9 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
     const float ry = R.ry, rz = R.rz;
     const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
     const float sig2 = R.sig2_u, eps24 = R.eps24_u;
-    int nband = 0;
-    bool tooclose = false;
+    // a pair within rounding of r_cut, or closer than the fixed-point range
+    // allows: both rare, so one flag, and the pass below tells them apart
+    bool rare = false;
     for (int k0 = 0; k0 < npad; k0 += kU) {
         int hh[kU];
 #pragma unroll
@@ -452,8 +453,8 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
             // padding entries are the particle itself (r^2 = 0)
             const bool nz0 = r2.x > 0.0f, nz1 = r2.y > 0.0f;
             const bool in0 = (r2.x < lo) & nz0, in1 = (r2.y < lo) & nz1;
-            nband += ((r2.x < hi) & !(r2.x < lo)) + ((r2.y < hi) & !(r2.y < lo));
-            tooclose |= ((r2.x < fmax2) & nz0) | ((r2.y < fmax2) & nz1);
+            rare |= ((r2.x < hi) & !(r2.x < lo)) | ((r2.y < hi) & !(r2.y < lo)) | ((r2.x < fmax2) & nz0) |
+                    ((r2.y < fmax2) & nz1);
             pair32x2<ENERGY>(dx, dy, dz, r2, in0, in1, sig2, eps24, a);
         }
     }
@@ -462,18 +463,21 @@ __device__ __forceinline__ void neighbours32(const Replica &R, const uint4 *hpos
         const unsigned bias = (unsigned)npad * kMagicBits;
         a.hx -= bias; a.lx -= bias; a.hy -= bias; a.ly -= bias; a.hz -= bias; a.lz -= bias;
     }
-    if (nband) {
+    if (rare) {
         // pairs within rounding of r_cut: membership decided in FP64 from the
-        // master positions, as in the FP64 reference
+        // master positions, as in the FP64 reference; and pairs too close for
+        // the fixed-point sums
+        bool tooclose = false;
         for (int k = 0; k < n; ++k) {
             const int h = checked_entry(ctl, nb[(long long)k * Pt], hsize, kSiteForceHalo);
             float dx, dy, dz, r2;
             sep_u<CUBIC>(pi, hpos[h], ry, rz, dx, dy, dz, r2);
+            tooclose |= (r2 < fmax2) & (r2 > 0.0f);
             if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, checked_slot(ctl, halo_slot(pc, np, h), S, i), R.L) < R.rc2)
                 pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, a);
         }
+        if (tooclose) err |= kErrFixed;
     }
-    if (tooclose) err |= kErrFixed;
 }
 
 // ---------------------------------------------------------------- half list
@@ -564,8 +568,9 @@ __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 
     const float ry = R.ry, rz = R.rz;
     const float lo = R.rc2_lo_u, hi = R.rc2_hi_u, fmax2 = R.fmax2_u;
     const float sig2 = R.sig2_u, eps24 = R.eps24_u;
-    int nband = 0;
-    bool tooclose = false;
+    // a pair within rounding of r_cut, or closer than the fixed-point range
+    // allows: both rare, so one flag, and the pass below tells them apart
+    bool rare = false;
     for (int k0 = 0; k0 < npad; k0 += kU) {
         int hh[kU];
 #pragma unroll
@@ -585,8 +590,8 @@ __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const bool nz0 = r2.x > 0.0f, nz1 = r2.y > 0.0f;
             const bool in0 = (r2.x < lo) & nz0, in1 = (r2.y < lo) & nz1;
-            nband += ((r2.x < hi) & !(r2.x < lo)) + ((r2.y < hi) & !(r2.y < lo));
-            tooclose |= ((r2.x < fmax2) & nz0) | ((r2.y < fmax2) & nz1);
+            rare |= ((r2.x < hi) & !(r2.x < lo)) | ((r2.y < hi) & !(r2.y < lo)) | ((r2.x < fmax2) & nz0) |
+                    ((r2.y < fmax2) & nz1);
             pair32x2_half<ENERGY>(dx, dy, dz, r2, in0, in1, sig2, eps24, a, Fq, S, q0.w, q1.w);
         }
     }
@@ -594,13 +599,15 @@ __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 
         const unsigned bias = (unsigned)npad * kMagicBits;
         a.hx -= bias; a.lx -= bias; a.hy -= bias; a.ly -= bias; a.hz -= bias; a.lz -= bias;
     }
-    if (nband) {
+    if (rare) {
+        bool tooclose = false;
         for (int k = 0; k < n; ++k) {
             const int h = checked_entry(ctl, nb[k * Pt], hsize, kSiteForceHalo);
             uint4 q = hpos[h];
             q.w = (unsigned)checked_slot(ctl, (int)q.w, S, i);
             float dx, dy, dz, r2;
             sep_u<CUBIC>(pi, q, ry, rz, dx, dy, dz, r2);
+            tooclose |= (r2 < fmax2) & (r2 > 0.0f);
             if (!(r2 < lo) && r2 < hi && r2_exact(X, S, i, (long long)q.w, R.L) < R.rc2) {
                 pair32<ENERGY>(dx, dy, dz, r2, true, sig2, eps24, a);
                 // the force scalar of pair32, for the partner's share
@@ -613,8 +620,8 @@ __device__ __forceinline__ void neighbours32_half(const Replica &R, const uint4 
                 red_sub(Fq + 2 * S + q.w, fx_value1(fs, dz));
             }
         }
+        if (tooclose) err |= kErrFixed;
     }
-    if (tooclose) err |= kErrFixed;
 }
 
 // Cosine angle term K (1 - cos theta) of a triple (a, b, c) with bond vectors
