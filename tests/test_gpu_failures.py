@@ -1,6 +1,8 @@
 """Failure detection and recovery, exercised without faulting the GPU.
 
 - A non-finite input is reported as MD_ERR_NONFINITE, and md_set_state clears it.
+- A pair closer than the FP32 path's fixed-point sums allow is reported as
+  MD_ERR_FIXED_OVERFLOW, with the full list and with the half list.
 - A bounded device wait that runs out is reported as MD_ERR_TIMEOUT, and the
   handle keeps working (the library's self-test waits on a barrier that
   nothing completes, with the same bounded wait as the tile kernels).
@@ -67,6 +69,36 @@ def test_nonfinite_state_is_reported_and_cleared(md, precision, which):
     b = state(md, h2, n)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+# ----------------------------------------------------------------- fixed-point range
+@pytest.mark.parametrize("half", [False, True])
+def test_too_close_pair_is_reported(md, half):
+    """FP32 + fixed point: one pair at r = 0.3 sigma, whose LJ force is beyond
+    the range of the fixed-point sums.  The pair loop flags the rare case and
+    the settling pass names it; a clean state afterwards gives the oracle's
+    forces."""
+    import oracle
+    from tests.helpers import force_rel_err
+    x, v, box = inputs.perturbed_lattice(5, seed=41, amp=0.05)
+    n = len(x)
+    bad = x.copy()
+    bad[1] = (bad[0] + np.array([0.3, 0.0, 0.0])) % box
+    h = md.md_create(n, box, precision=1)
+    md.md_set_half_list(h, half)
+    md.md_set_state(h, dev(bad), dev(v))
+    md.md_build_neighbors(h)
+    f = torch.zeros(3, n, dtype=torch.float64, device="cuda")
+    md.md_compute_forces(h, f, None)
+    with pytest.raises(md.MDError) as e:
+        md.md_sync(h)
+    assert e.value.status == md.MD_ERR_FIXED_OVERFLOW
+    md.md_set_state(h, dev(x), dev(v))
+    md.md_build_neighbors(h)
+    md.md_compute_forces(h, f, None)
+    md.md_sync(h)
+    Fo, _ = oracle.forces(oracle.System(n, box, rc=2.5), x, v)
+    assert force_rel_err(host(f), Fo) <= 1e-5
 
 
 # ----------------------------------------------------------------- bounded waits
