@@ -331,13 +331,22 @@ __device__ void finish(const Bufs &b, bool drifted, bool energy, bool tiled, flo
 // `in`, and the fixed-point accumulation of force, energy and virial.
 struct Acc32 {
     unsigned hx, lx, hy, ly, hz, lz;
-    // energies: sums over the interacting pairs of s6 (s6 - 1) and
-    // s6 (2 s6 - 1) (s6 = (sigma/r)^6) and their count, so that the pair
-    // energy is 4 eps su - n V(r_cut) and the virial 24 eps sg; two partial
-    // sums each (the lanes of the packed loop), added at the end
-    float2 su, sg;
+    // energies: sums over the interacting pairs of s6 = (sigma/r)^6 and of
+    // g = s6 (2 s6 - 1), and their count.  s6 (s6 - 1) = (g - s6) / 2, so the
+    // pair energy is 2 eps (sg - s6) - n V(r_cut) and the virial 24 eps sg.
+    // Two partial sums each (the lanes of the packed loop), added at the end;
+    // the packed loop counts in FP32 as r^2 times its masked 1/r^2 (1 to
+    // rounding per interacting pair, 0 otherwise), the single-pair path in nin.
+    float2 s6, sg, cnt;
     int nin;
 };
+
+// The shifted LJ energy summed over the pairs of these sums: 4 eps times the
+// sum of s6 (s6 - 1), minus V(r_cut) per interacting pair (FP32).
+__device__ __forceinline__ float pair_energy(const Replica &R, const Acc32 &a)
+{
+    return R.eps4_f * 0.5f * ((a.sg.x + a.sg.y) - (a.s6.x + a.s6.y)) - R.vshift_f * ((a.cnt.x + a.cnt.y) + (float)a.nin);
+}
 
 // slot of halo index h (pieces are in ascending halo order)
 __device__ __forceinline__ int halo_slot(const Piece *pc, int np, int h)
@@ -376,7 +385,7 @@ __device__ __forceinline__ void pair32(float dx, float dy, float dz, float r2, b
     fx_acc2(fs, dy, a.hy, a.ly);
     fx_acc2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        a.su.x += in ? __fmaf_rn(s6, s6, -s6) : 0.0f;
+        a.s6.x += in ? s6 : 0.0f;
         a.sg.x += in ? g : 0.0f;
         a.nin += in ? 1 : 0;
     }
@@ -401,10 +410,9 @@ __device__ __forceinline__ void pair32x2(float2 dx, float2 dy, float2 dz, float2
     fx_acc2x2(fs, dy, a.hy, a.ly);
     fx_acc2x2(fs, dz, a.hz, a.lz);
     if (ENERGY) {
-        const float2 e = __ffma2_rn(s6, s6, make_float2(-s6.x, -s6.y));   // s6 (s6 - 1)
-        a.su = __fadd2_rn(a.su, e);
+        a.s6 = __fadd2_rn(a.s6, s6);
         a.sg = __fadd2_rn(a.sg, g);
-        a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+        a.cnt = __ffma2_rn(ir2, r2, a.cnt);
     }
 }
 
@@ -550,10 +558,9 @@ __device__ __forceinline__ void pair32x2_half(float2 dx, float2 dy, float2 dz, f
     if (in0) { red_sub(Fq + s0, x0); red_sub(Fq + S + s0, y0); red_sub(Fq + 2 * S + s0, z0); }
     if (in1) { red_sub(Fq + s1, x1); red_sub(Fq + S + s1, y1); red_sub(Fq + 2 * S + s1, z1); }
     if (ENERGY) {
-        const float2 e = __ffma2_rn(s6, s6, make_float2(-s6.x, -s6.y));   // s6 (s6 - 1)
-        a.su = __fadd2_rn(a.su, e);
+        a.s6 = __fadd2_rn(a.s6, s6);
         a.sg = __fadd2_rn(a.sg, g);
-        a.nin += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+        a.cnt = __ffma2_rn(ir2, r2, a.cnt);
     }
 }
 
@@ -833,7 +840,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 fscale = kFixInv;
                 ckick = b.half_dt_over_m_fix;
             } else if (PREC == 1) {
-                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
+                Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
                 if (lstaged) {
                     const unsigned short *nbs = lst + (i - tl.s0);
                     if (R.cubic) neighbours32<ENERGY, true, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.ctl, pc[np].hoff);
@@ -850,7 +857,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 1 ? MDK_FORCE_MIN_BLOCKS : 1) 
                 ckick = b.half_dt_over_m_fix;
                 if (ENERGY) {
                     // twice this particle's pair energy and virial, in FP32, to fixed point
-                    uf += fx_round(R.eps4_f * (a.su.x + a.su.y) - R.vshift_f * (float)a.nin);
+                    uf += fx_round(pair_energy(R, a));
                     wf += fx_round(R.eps24_f * (a.sg.x + a.sg.y));
                 }
             } else {
@@ -1185,7 +1192,7 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
             // a list block too long for the stage is read from global memory
             // through the same [row][particle] layout
             const unsigned short *nbs = lstaged ? lst + (i - tl.s0) : b.nbr + nbr_index(tl.s0, Pt, b.K, 0, (int)(i - tl.s0));
-            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
+            Acc32 a = {0u, 0u, 0u, 0u, 0u, 0u, make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f), 0};
             if (R.cubic) neighbours32_half<ENERGY, true>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq, b.ctl,
                                                   pc[np].hoff);
             else neighbours32_half<ENERGY, false>(R, hpos, nbs, Pt, n, npad, pi, X, b.S, i, pc, np, a, err, b.Fq, b.ctl,
@@ -1199,7 +1206,7 @@ __global__ void __launch_bounds__(kBlock, MDK_FORCE_MIN_BLOCKS) k_pairs_half(Buf
             if (ENERGY) {
                 // each pair once here: twice its energy and virial, as the
                 // full list's two visits give
-                uf += fx_round(2.0f * (R.eps4_f * (a.su.x + a.su.y) - R.vshift_f * (float)a.nin));
+                uf += fx_round(2.0f * pair_energy(R, a));
                 wf += fx_round(2.0f * (R.eps24_f * (a.sg.x + a.sg.y)));
             }
         }
